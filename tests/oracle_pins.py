@@ -1,0 +1,260 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Each pin takes the path of an oracle build so that the mutation test can run
+the same pins against deliberately broken builds (tests/test_oracle_mutants.py).
+
+What pins what:
+  class map          closed form ceil(log2 n) - 4 over every n in [0, chunk+1]
+  layout / address   a single-class fill of a tiny heap returns exactly the
+                     multiples of the page size in [0, bytes)
+  capacity           closed form n_chunks * chunk / page; page-array limit
+                     floor(min(bytes/page, cap) / ppc) * ppc
+  queue semantics    brute force against a set allocator (tests/setmodel.py)
+  small workload     closed form of the 10,240 x 16 B run (tests/golden/c0_small.json)
+  restore            free everything, trim: the state equals the post-create state
+  queue segments     closed form of segment use for a fill that ends on a segment edge
+  fmix32             MurmurHash3 reference vectors (tests/golden/murmur3_fmix32.json)
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+
+import oracle
+from setmodel import SetModel, ceil_log2
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+ALL_VARIANTS = ("page_array", "chunk_array", "page_vlist", "chunk_vlist")
+
+
+def heap(lib_path, bytes_, chunk, variant, cap=0):
+    return oracle.OracleHeap(bytes_, chunk, variant, cap, lib_path=lib_path)
+
+
+def pin_class_map(lib_path):
+    lib = oracle.load(lib_path)
+    for chunk in (256, 1024, 8192, 65536, 1 << 20):
+        assert lib.orc_num_classes(chunk) == ceil_log2(chunk) - 3
+        ns = range(0, chunk + 2) if chunk <= 65536 else \
+            list(range(0, 4097)) + [chunk - 1, chunk, chunk + 1] + [2 ** k + d for k in range(5, 20) for d in (-1, 0, 1)]
+        for n in ns:
+            c = lib.orc_size_class(chunk, n)
+            if n == 0 or n > chunk:
+                assert c == -1, (chunk, n, c)
+            else:
+                assert c == max(0, ceil_log2(n) - 4), (chunk, n, c)
+                pb = lib.orc_page_bytes(c)
+                assert pb >= n and (pb == 16 or pb // 2 < n)
+
+
+def pin_layout(lib_path):
+    """Every class of every variant: filling a tiny heap with one class hands
+    out each page-aligned block exactly once and then returns null."""
+    for variant in ALL_VARIANTS:
+        for chunk in (256, 512):
+            bytes_ = 8 * chunk
+            for c in range(ceil_log2(chunk) - 3):
+                page = 16 << c
+                h = heap(lib_path, bytes_, chunk, variant)
+                offs = []
+                while True:
+                    o = h.malloc(page)
+                    if o < 0:
+                        break
+                    offs.append(o)
+                    assert len(offs) <= bytes_ // page
+                st = h.stats()
+                if variant.endswith("array"):
+                    assert sorted(offs) == list(range(0, bytes_, page)), (variant, chunk, c)
+                else:
+                    # queue segments take whole chunks out of the same heap
+                    segs = st["seg_chunks"] + st["spare_chunks"]
+                    assert segs >= 1
+                    assert len(offs) == (bytes_ // chunk - segs) * (chunk // page), (variant, c)
+                    assert len(set(offs)) == len(offs)
+                    assert all(o % page == 0 for o in offs)
+                assert st["mallocs"][c] == len(offs) and st["failed"][c] == 1
+                assert st["carved_now"][c] * (chunk // page) == len(offs)
+
+
+def pin_capacity(lib_path):
+    # plain capacity: n_chunks * pages per chunk
+    for variant in ("page_array", "chunk_array"):
+        h = heap(lib_path, 64 * 1024, 1024, variant)
+        got = sum(1 for _ in range(5000) if h.malloc(48) >= 0)
+        assert got == (64 * 1024) // 64, (variant, got)
+    # page-array queue capacity min(bytes/page, cap), rounded down to whole chunks
+    for cap in (100, 512, 1000, 4096):
+        h = heap(lib_path, 64 * 1024, 1024, "page_array", cap)
+        got = sum(1 for _ in range(5000) if h.malloc(16) >= 0)
+        qc = min(64 * 1024 // 16, cap)
+        assert got == (qc // 64) * 64, (cap, got)
+
+
+def _run_sequence(lib_path, variant, bytes_, chunk, ops, model_nulls=True):
+    """Apply ops to the oracle and the set model; compare after every op.
+    model_nulls=False (virtualized queues, whose segments hold chunks of the
+    same heap): blocks and counts are checked, null answers only counted."""
+    h = heap(lib_path, bytes_, chunk, variant)
+    m = SetModel(bytes_, chunk)
+    order = []   # live offsets in allocation order
+    freed = []   # offsets freed at least once
+    for op, arg in ops:
+        if op == "m":
+            o = h.malloc(arg)
+            c = m.cls(arg)
+            if o >= 0 or model_nulls or c is None:
+                m.check_malloc(arg, o)
+            else:
+                m.failed[c] += 1
+            if o >= 0:
+                order.append(o)
+        elif op == "f":
+            if not order:
+                continue
+            o = order.pop(arg % len(order))
+            assert h.free(o) == 0
+            m.free(o)
+            freed.append(o)
+        elif op == "d":     # free a block a second time (unless it was handed out again)
+            if not freed:
+                continue
+            o = freed[arg % len(freed)]
+            want = m.expected_free_error(o)
+            if want:
+                assert h.free(o) == want, (o, want)
+        elif op == "x":     # a pointer that is not a block start
+            want = m.expected_free_error(arg)
+            assert h.free(arg) == want, (arg, want)
+        elif op == "t":
+            h.trim()
+            m.trim()
+        st = h.stats()
+        if st["error_bits"] & oracle.ERR_QUEUE_FULL:
+            # a virtualized queue found no chunk for a segment and dropped the
+            # freed page: the set model no longer applies from here on
+            assert not model_nulls
+            return h, m
+        for c in range(len(m.mallocs)):
+            assert st["mallocs"][c] == m.mallocs[c]
+            assert st["frees"][c] == m.frees[c]
+            assert st["failed"][c] == m.failed[c]
+            assert st["live"][c] == m.mallocs[c] - m.frees[c]
+            assert st["carved_now"][c] == m.owner.count(c)
+    return h, m
+
+
+def pin_brute_force(lib_path, max_len=4, random_runs=60, random_len=250):
+    sizes = (0, 1, 16, 17, 33, 100, 256, 257)
+    alphabet = [("m", s) for s in sizes] + [("f", 0), ("f", 1), ("d", 0), ("x", 8), ("x", 1 << 20),
+                                            ("t", 0)]
+    for variant in ("page_array", "chunk_array"):
+        for L in range(1, max_len + 1):
+            for ops in itertools.product(alphabet, repeat=L):
+                _run_sequence(lib_path, variant, 2 * 256, 256, ops)
+    rng = np.random.default_rng(20250424)
+    for variant in ALL_VARIANTS:
+        nulls = variant.endswith("array")
+        for _ in range(random_runs):
+            ops = []
+            for _ in range(random_len):
+                r = rng.random()
+                if r < 0.55:
+                    ops.append(("m", int(rng.choice([1, 16, 20, 32, 50, 64, 120, 128, 200, 256]))))
+                elif r < 0.90:
+                    ops.append(("f", int(rng.integers(0, 1000))))
+                elif r < 0.93:
+                    ops.append(("d", int(rng.integers(0, 1000))))
+                elif r < 0.97:
+                    ops.append(("x", int(rng.integers(0, 4 * 256)) | 1))
+                else:
+                    ops.append(("t", 0))
+            chunk, nch = (256, 6) if nulls else (512, 12)
+            _run_sequence(lib_path, variant, nch * chunk, chunk, ops, model_nulls=nulls)
+
+
+def pin_small_workload(lib_path):
+    g = json.load(open(os.path.join(GOLDEN, "c0_small.json")))
+    h = heap(lib_path, g["heap_bytes"], g["chunk_bytes"], "page_array")
+    sizes = np.full(g["threads"], g["request_bytes"], np.uint32)
+    res, offs = h.round(sizes, seed=0, mode=0, return_offsets=True)
+    st = h.stats()
+    assert res["nulls"] == 0 and res["mismatches"] == 0
+    assert res["xor64"] == g["xor_of_thread_ids"] and res["sum64"] == g["sum_of_thread_ids"]
+    assert st["carves"][g["class"]] == g["chunks_carved"]
+    assert st["queued"][g["class"]] == g["queued_after_free_all"]
+    assert sorted(offs.tolist()) == list(range(0, g["threads"] * 16, 16))
+    assert st["mallocs"][0] == st["frees"][0] == g["threads"] and st["live"][0] == 0
+
+
+def _post_create(lib_path, variant, bytes_, chunk):
+    return heap(lib_path, bytes_, chunk, variant).canonical_state()
+
+
+def _same_state(a, b):
+    assert a["bump"] == b["bump"], (a["bump"], b["bump"])
+    assert np.array_equal(a["pool"], b["pool"])
+    assert np.array_equal(a["chunk_cls"], b["chunk_cls"])
+    for qa, qb in zip(a["queues"], b["queues"]):
+        assert np.array_equal(qa, qb)
+
+
+def pin_restore(lib_path):
+    rng = np.random.default_rng(7)
+    for variant in ALL_VARIANTS:
+        bytes_, chunk = 8 << 20, 4096        # roomy: no request fails, no segment is refused
+        h = heap(lib_path, bytes_, chunk, variant)
+        live = []
+        for _ in range(3000):
+            if rng.random() < 0.6 or not live:
+                o = h.malloc(int(rng.integers(1, chunk + 1)))
+                assert o >= 0
+                if o >= 0:
+                    live.append(o)
+            else:
+                assert h.free(live.pop(int(rng.integers(0, len(live))))) == 0
+        rng.shuffle(live)
+        for o in live:
+            assert h.free(o) == 0
+        h.trim()
+        st = h.stats()
+        assert sum(st["live"]) == 0 and st["error_bits"] == 0
+        _same_state(h.canonical_state(), _post_create(lib_path, variant, bytes_, chunk))
+    # a partial trim keeps live chunks and returns only the all-free ones
+    h = heap(lib_path, 64 * 4096, 4096, "page_array")
+    a = [h.malloc(16) for _ in range(256 * 3)]          # three chunks of class 0
+    for o in a[256:]:
+        h.free(o)
+    h.trim()
+    st = h.stats()
+    assert st["carved_now"][0] == 1 and st["queued"][0] == 0 and st["bump"] == 1
+
+
+def pin_segments(lib_path):
+    """Virtualized queue storage (Sec. 4.3) under the stated rule: a segment is
+    one chunk holding (chunk - 64) / 8 cells, and it retires only once every
+    position in it was consumed and a successor exists.  Closed form with
+    512 B chunks (56 cells) and 64 B requests (8 pages per chunk): 56 requests
+    use 7 data chunks and exactly fill segment 0; the 57th needs segment 1."""
+    h = heap(lib_path, 64 * 512, 512, "page_vlist")
+    for _ in range(56):
+        assert h.malloc(64) >= 0
+    st = h.stats()
+    assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == (1, 0, 8), st
+    assert h.malloc(64) >= 0
+    st = h.stats()
+    assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == (1, 1, 10), st
+
+
+def pin_fmix32(lib_path):
+    lib = oracle.load(lib_path)
+    g = json.load(open(os.path.join(GOLDEN, "murmur3_fmix32.json")))
+    for v in g["vectors"]:
+        assert lib.orc_fmix32(int(v["seed"], 16)) == int(v["hash"], 16)
+
+
+ALL_PINS = (pin_class_map, pin_layout, pin_capacity, pin_brute_force, pin_small_workload,
+            pin_restore, pin_segments, pin_fmix32)

@@ -1,0 +1,83 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each mutant is a one-line change to a copy of oracle/ouro_oracle.c (a dropped
+term, a wrong index, an off-by-one, a swapped operand), compiled on the CPU
+into a temporary library.  The pins of tests/oracle_pins.py run against it and
+at least one of them must fail.  The real oracle is never modified.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "ouro_oracle.c")
+
+MUTANTS = {
+    "class_off_by_one": ("while (orc_page_bytes(c) < n) c++;", "while (orc_page_bytes(c) <= n) c++;"),
+    "pages_per_chunk_halved": ("return h->chunk_bytes / orc_page_bytes(c);",
+                               "return h->chunk_bytes / orc_page_bytes(c) / 2;"),
+    "page_address_scale": ("off = id * pb;", "off = id * 16;"),
+    "free_pushes_wrong_id": ("q_push(h, c, off / pb);", "q_push(h, c, off / 16);"),
+    "chunk_not_requeued": ("if (h->free_pages[x] == 1) q_push(h, c, x);",
+                           "if (h->free_pages[x] == 0) q_push(h, c, x);"),
+    "trim_keeps_bump": ("while (np && pv[np - 1] == h->bump - 1) { np--; h->bump--; }", ""),
+    "chunk_claims_wrong_bit": ("w[p >> 6] &= ~(1ull << (p & 63));", "w[p >> 6] &= ~(1ull << ((p + 1) & 63));"),
+    "no_double_free_check": ("if (!live_get(h, off))", "if (0)"),
+    "bump_past_end": ("if (h->bump < h->n_chunks) return", "if (h->bump <= h->n_chunks) return"),
+    "page_array_cap_ignored": ("if ((h->carved_now[c] + 1) * ppc > qc) return -1;", ""),
+    "segment_retired_early": ("while (h->segs[c].n >= 2 && h->qhead[c]", "while (h->segs[c].n >= 1 && h->qhead[c]"),
+    "trim_reclaims_partial": ("if (fr == ppc) reclaim[x] = 1;", "if (fr + 1 >= ppc) reclaim[x] = 1;"),
+    "chunk_full_not_popped": ("if (h->free_pages[x] == 0) q_pop(h, c);", ""),
+    "fmix_shift": ("x ^= x >> 13;", "x ^= x >> 12;"),
+}
+
+
+def _build_mutant(name, old, new, tmpdir):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    path = os.path.join(tmpdir, f"ouro_oracle_{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    # the mutant compiles beside a copy of the header
+    with open(os.path.join(tmpdir, "ouro_oracle.h"), "w") as f:
+        f.write(open(SRC.replace(".c", ".h")).read())
+    lib = os.path.join(tmpdir, f"lib_{name}.so")
+    subprocess.run(["gcc", "-O1", "-std=c11", "-w", "-shared", "-fPIC", "-o", lib, path], check=True)
+    return lib
+
+
+_RUNNER = """
+import sys
+sys.path[:0] = [{root!r}, {tests!r}]
+import oracle_pins as P
+pin = getattr(P, {pin!r})
+if {pin!r} == "pin_brute_force":
+    pin({lib!r}, max_len=3, random_runs=25, random_len=200)
+else:
+    pin({lib!r})
+"""
+
+
+def _pin_fails(pin_name, lib):
+    """Run one pin in a child process: a planted mistake may crash or loop."""
+    tests = os.path.dirname(os.path.abspath(__file__))
+    code = _RUNNER.format(root=os.path.dirname(tests), tests=tests, pin=pin_name, lib=lib)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, timeout=120)
+    except subprocess.TimeoutExpired:
+        return True
+    return r.returncode != 0
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name):
+    old, new = MUTANTS[name]
+    with tempfile.TemporaryDirectory() as d:
+        lib = _build_mutant(name, old, new, d)
+        caught = next((p.__name__ for p in P.ALL_PINS if _pin_fails(p.__name__, lib)), None)
+        assert caught, f"mutant {name} passed every pin"
