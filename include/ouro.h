@@ -1,0 +1,218 @@
+/*
+ * ouro.h -- C ABI of the GB300 device-side dynamic memory allocator.
+ *
+ * The method follows "Dynamic Memory Management on GPUs with SYCL"
+ * (arXiv 2504.18211), which ports the Ouroboros allocator:
+ *   - the host preallocates one block of device memory to act as a heap and
+ *     an allocation algorithm runs on the device (Sec. 1, Introduction);
+ *   - the heap is divided into chunks; requests are served as pages from
+ *     inside chunks, through one lock-free queue per size (Sec. 1; Sec. 4);
+ *   - sizes are powers of two (Sec. 4.2);
+ *   - page queues hand out fixed-size pages (Sec. 4.1); chunk queues hold
+ *     chunks with free pages, which are scanned for a free page (Sec. 4.2);
+ *   - virtualized queues keep their storage inside the heap (Sec. 4.3);
+ *   - the driver round allocates, writes, reads back and frees (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   - return an ouro_status (0 = OURO_OK); no entry point aborts or traps;
+ *   - "d_" arguments are DEVICE pointers owned by the caller; "h_"/"out"
+ *     arguments are HOST pointers owned by the caller;
+ *   - calls taking a cudaStream_t are asynchronous on that stream unless the
+ *     comment says "syncs"; a NULL stream is the legacy default stream;
+ *   - OURO_ECUDA keeps the CUDA error in ouro_last_cuda_error().
+ * Device-side use (ouro_malloc / ouro_free inside user kernels) is declared
+ * in ouro_device.cuh.
+ */
+#ifndef OURO_H
+#define OURO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ouro_status;
+enum {
+  OURO_OK = 0,
+  OURO_EINVAL = 1,    /* bad argument */
+  OURO_ENOMEM = 2,    /* a host or device allocation failed */
+  OURO_ECUDA = 3,     /* a CUDA call failed; see ouro_last_cuda_error() */
+  OURO_EDEVICE = 4,   /* the heap's device error word is non-zero (see ouro_stats.error_bits) */
+  OURO_ENOTSUP = 5    /* the heap's variant does not offer this operation */
+};
+
+/* queue variants: page or chunk queues (Sec. 4.1, 4.2), array or virtualized list (Sec. 4.3) */
+typedef enum {
+  OURO_PAGE_ARRAY = 0,
+  OURO_CHUNK_ARRAY = 1,
+  OURO_PAGE_VLIST = 2,
+  OURO_CHUNK_VLIST = 3
+} ouro_variant;
+
+/* device error bits (sticky until ouro_heap_reset) */
+enum {
+  OURO_ERR_BAD_FREE = 1u << 0,       /* pointer outside the heap, unaligned or in an uncarved chunk */
+  OURO_ERR_DOUBLE_FREE = 1u << 1,    /* page already free (chunk queues; page queues when checked) */
+  OURO_ERR_QUEUE_FULL = 1u << 2,     /* a virtualized queue needed a segment and no chunk was left */
+  OURO_ERR_TIMEOUT = 1u << 3,        /* a bounded wait ran out; the request returned null */
+  OURO_ERR_QUEUE_OVERFLOW = 1u << 4  /* a queue slot stayed busy for a whole lap */
+};
+
+#define OURO_MAX_CLASSES 17            /* 16 B .. 1 MiB */
+
+typedef struct ouro_heap ouro_heap;   /* host handle, opaque */
+
+typedef struct {
+  uint32_t spin_limit;            /* iterations of a bounded wait before it gives up (default 1<<20) */
+  uint32_t backoff_min_ns;        /* first __nanosleep of a waiting warp (default 32) */
+  uint32_t backoff_max_ns;        /* backoff cap (default 2048) */
+  uint32_t max_carve;             /* chunks one carve may take at once (default 65536) */
+  uint64_t array_queue_capacity;  /* page-array item limit per class (default 1<<23) */
+  uint32_t checked;               /* page queues: track live pages to detect double frees */
+  uint32_t reserved;
+} ouro_options;
+
+/* Device view of a heap, passed BY VALUE to kernels that call ouro_malloc /
+ * ouro_free.  Filled by ouro_heap_device(); its pointers stay valid until
+ * ouro_heap_destroy().  The pointed-to layouts are private to the library. */
+typedef struct {
+  unsigned char *base;
+  unsigned long long bytes, n_chunks;
+  unsigned int chunk_bytes, log2_chunk, n_classes, variant;
+  unsigned int seg_cap, words_per_chunk;
+  unsigned int spin_limit, backoff_min_ns, backoff_max_ns, max_carve;
+  unsigned int checked, pad0;
+  void *qhdr;                          /* per-class queue headers */
+  unsigned long long *cells;           /* array variants: every class ring, back to back */
+  unsigned long long ring_off[OURO_MAX_CLASSES];
+  unsigned long long ring_mask[OURO_MAX_CLASSES];
+  unsigned long long qcap[OURO_MAX_CLASSES];   /* page-array item limit per class */
+  unsigned char *chunk_cls;            /* class of each chunk; 0xFF none, 0xFE queue segment */
+  int *chunk_free;                     /* chunk queues: free pages per chunk */
+  unsigned int *bits;                  /* free-page bitmap (chunk queues; checked page queues) */
+  unsigned int *pool;                  /* chunk ids returned by ouro_heap_trim */
+  void *glob;                          /* heap-wide counters and error word */
+  unsigned long long *stats;           /* sharded per-class counters */
+} ouro_heap_dev;
+
+typedef struct {
+  uint64_t mallocs[OURO_MAX_CLASSES];     /* successful device mallocs */
+  uint64_t frees[OURO_MAX_CLASSES];       /* successful device frees */
+  uint64_t failed[OURO_MAX_CLASSES];      /* null returns for a request with a class */
+  uint64_t carves[OURO_MAX_CLASSES];      /* chunks ever carved for the class */
+  uint64_t carved_now[OURO_MAX_CLASSES];  /* chunks the class owns now (chunk table) */
+  uint64_t queued[OURO_MAX_CLASSES];      /* queue entries (quiescent heaps only) */
+  uint64_t live[OURO_MAX_CLASSES];        /* mallocs - frees */
+  uint64_t repushes[OURO_MAX_CLASSES];    /* items re-queued after a consumer gave up a slot */
+  uint64_t dead[OURO_MAX_CLASSES];        /* queue positions answered with null (heap exhausted) */
+  uint64_t zero_reqs, too_large;          /* requests of 0 bytes / above one chunk */
+  uint64_t bump, pool_size, seg_chunks, spare_chunks;
+  uint32_t error_bits, n_classes;
+} ouro_stats;
+
+/* Host copy of the queue state, for tests (ouro_heap_snapshot).  Arrays are
+ * malloc'ed by the library and released by ouro_snapshot_free. */
+typedef struct {
+  uint32_t n_classes;
+  uint64_t n_chunks;
+  uint64_t bump;
+  uint64_t pool_n;
+  uint32_t *pool;                        /* pool_n chunk ids, in pool order */
+  uint8_t *chunk_cls;                    /* n_chunks entries */
+  int32_t *chunk_free;                   /* n_chunks entries (chunk queues) or NULL */
+  uint64_t queue_n[OURO_MAX_CLASSES];
+  uint32_t *queue[OURO_MAX_CLASSES];     /* items from head to tail, null answers skipped */
+} ouro_snapshot;
+
+/* ---- heap life cycle (Sec. 1: the host preallocates the heap) ---------- */
+
+/* Create a heap of `bytes` bytes cut into chunks of `chunk_bytes` with
+ * page-array queues and default options.  chunk_bytes: power of two in
+ * [256 B, 1 MiB]; bytes: a multiple of chunk_bytes, at most 64 GiB.
+ * *out receives the handle.  EINVAL on bad sizes, ENOMEM/ECUDA on
+ * allocation failure (nothing is leaked). */
+ouro_status ouro_heap_create(size_t bytes, size_t chunk_bytes, ouro_heap **out);
+
+/* As ouro_heap_create with a queue variant, options (NULL = defaults) and
+ * optionally a caller-owned device buffer of `bytes` bytes used as the heap
+ * (NULL = the library allocates and owns it).  A caller buffer must be
+ * 256-byte aligned and outlive the heap. */
+ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, ouro_variant variant,
+                                const ouro_options *opt, void *d_heap_buf, ouro_heap **out);
+
+/* Release every device buffer the heap owns.  NULL is accepted.  Syncs the device. */
+ouro_status ouro_heap_destroy(ouro_heap *h);
+
+/* Back to the post-create state: every chunk uncarved, queues empty, counters
+ * and error word cleared.  Quiescent: no kernel may use the heap meanwhile. */
+ouro_status ouro_heap_reset(ouro_heap *h, void *stream);
+
+/* Quiescent reclaim: every chunk whose pages are all free leaves its class
+ * queue and returns to the pool; the pool is sorted; the bump pointer drops
+ * over pooled chunks at its top; virtualized queues are re-laid from
+ * position 0.  After freeing everything, the state equals the post-create
+ * state.  Syncs `stream`. */
+ouro_status ouro_heap_trim(ouro_heap *h, void *stream);
+
+/* Fill *out with the device view used by ouro_malloc / ouro_free. */
+ouro_status ouro_heap_device(const ouro_heap *h, ouro_heap_dev *out);
+
+/* Read and sum the device counters.  Syncs `stream`.  Returns OURO_EDEVICE
+ * (after filling *out) when the device error word is non-zero. */
+ouro_status ouro_heap_stats(ouro_heap *h, ouro_stats *out, void *stream);
+
+/* Copy the queue state to host arrays (tests).  Quiescent; syncs `stream`. */
+ouro_status ouro_heap_snapshot(ouro_heap *h, ouro_snapshot *out, void *stream);
+void ouro_snapshot_free(ouro_snapshot *s);
+
+/* ---- batch API (one device thread per request) --------------------------- */
+
+/* d_ptrs[i] = ouro_malloc(d_sizes[i]) for i < n; null for failures. */
+ouro_status ouro_batch_malloc(ouro_heap *h, const uint32_t *d_sizes, void **d_ptrs, size_t n,
+                              void *stream);
+/* ouro_free(d_ptrs[i]) for i < n; null entries are skipped. */
+ouro_status ouro_batch_free(ouro_heap *h, void *const *d_ptrs, size_t n, void *stream);
+
+/* ---- driver round payload (Sec. 3: write data, read it back, check) ------ */
+
+/* Result of a read-back check, written to device memory by the kernels. */
+typedef struct {
+  unsigned long long nulls;       /* requests that got null */
+  unsigned long long mismatches;  /* words or tail bytes that read back wrong */
+  unsigned long long xor64;       /* XOR of every word read back */
+  unsigned long long sum64;       /* wrapping sum of every word read back */
+  unsigned long long words;       /* words checked (a partial tail counts as one) */
+} ouro_check;
+
+/* Pattern of request i: mode 0 writes i into word 0; mode 1 writes
+ * floor(size/4) words key_i + w * 0x9E3779B9 (key_i = fmix32(seed ^
+ * i * 0x9E3779B9)) and the low size%4 bytes of the next word. */
+ouro_status ouro_pattern_write(void *const *d_ptrs, const uint32_t *d_sizes, size_t n,
+                               uint32_t seed, int mode, void *stream);
+/* Read every block back; *d_out (device) is overwritten with the result. */
+ouro_status ouro_pattern_check(void *const *d_ptrs, const uint32_t *d_sizes, size_t n,
+                               uint32_t seed, int mode, ouro_check *d_out, void *stream);
+
+/* One whole driver round in ONE kernel: every request allocates, writes its
+ * pattern, reads it back and frees.  *d_out (device) receives the check.
+ * d_ptrs (device, optional): receives each request's block address. */
+ouro_status ouro_round_fused(ouro_heap *h, const uint32_t *d_sizes, size_t n, uint32_t seed,
+                             int mode, ouro_check *d_out, void **d_ptrs, void *stream);
+
+/* ---- misc ----------------------------------------------------------------- */
+const char *ouro_status_string(ouro_status s);
+int ouro_last_cuda_error(void);
+/* Number of the library's kernels launched since load (a running count). */
+uint64_t ouro_kernel_launches(void);
+
+/* Test aid: advance the producer counter of class `cls` by n without filling
+ * the slots, so that the consumers of those slots wait until their bounded
+ * wait gives up (OURO_ERR_TIMEOUT) -- used to test liveness without a fault. */
+ouro_status ouro_debug_stall_producer(ouro_heap *h, int cls, uint32_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,722 @@
+/*
+ * ouro_device.cuh -- device-side ouro_malloc / ouro_free (sm_103a).
+ *
+ * Include from any kernel; pass the heap's ouro_heap_dev (ouro_heap_device())
+ * by value.  Any subset of a warp may call in divergent code.  Results are
+ * aligned to their power-of-two class (at least 16 B).  No call traps or
+ * waits without bound: a wait that runs out answers null and sets
+ * OURO_ERR_TIMEOUT in the heap's error word.
+ *
+ * Method (arXiv 2504.18211, which ports Ouroboros):
+ *   - one preallocated heap cut into chunks; requests are served as pages
+ *     of a chunk, through one lock-free queue per power-of-two size
+ *     (Sec. 1; Sec. 4 preamble; Sec. 4.2);
+ *   - page queues hand out fixed-size pages (Sec. 4.1);
+ *   - virtualized queues keep their slots inside heap chunks (Sec. 4.3);
+ *   - lanes of a warp that ask for the same size are served together by one
+ *     queue operation, with the active mask deciding who takes part
+ *     (Sec. 2, warp votes masked by the active mask);
+ *   - waiting threads are throttled with nanosleep (Sec. 2).
+ *
+ * GB300 design (not in the paper):
+ *   - a queue slot is one 64-bit word {sequence, item}; positions come from
+ *     two monotone 64-bit counters (head for consumers, tail for producers),
+ *     so a warp group needs ONE atomic on head (malloc) or tail (free) and its
+ *     lanes then touch consecutive slots (coalesced);
+ *   - a consumer whose position is beyond the producers is "in debt": the
+ *     one lane per class that takes the class carve lock carves every chunk
+ *     the current debt needs in one batch, and its whole warp writes the new
+ *     page ids into the slots;
+ *   - when the heap has no chunk left, the remaining debt positions are
+ *     answered with a null marker, so a full heap returns null exactly as
+ *     often as a sequential allocator would in a malloc-only phase.
+ */
+#ifndef OURO_DEVICE_CUH
+#define OURO_DEVICE_CUH
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ouro.h"
+
+#define OURO_NIL 0xFFFFFFFFu
+#define OURO_CLS_NONE 0xFFu
+#define OURO_CLS_SEG 0xFEu
+#define OURO_VL_HINTS 64
+#define OURO_NSTAT 8
+#define OURO_SHARDS 32
+#define OURO_SEG_HDR 64
+
+enum {
+  OURO_ST_MALLOC = 0, OURO_ST_FREE = 1, OURO_ST_FAILED = 2, OURO_ST_CARVE = 3,
+  OURO_ST_REPUSH = 4, OURO_ST_CANCEL = 5, OURO_ST_DEAD = 6, OURO_ST_SEG = 7
+};
+/* stats row n_classes holds requests without a class */
+enum { OURO_ST_ZERO = 0, OURO_ST_TOO_LARGE = 1 };
+
+/* one hot counter per 128-byte line */
+struct __align__(128) ouro_line {
+  unsigned long long v;
+  unsigned long long pad[15];
+};
+
+struct ouro_qhdr {
+  ouro_line head;    /* next consumer position */
+  ouro_line tail;    /* next producer position */
+  ouro_line lock;    /* carve lock: 0 free, 1 held */
+  ouro_line carved;  /* chunks owned by the class (page-array capacity) */
+  ouro_line front;   /* virtualized list: oldest live segment (idx << 32 | chunk) */
+  ouro_line back;    /* virtualized list: newest segment (hint) */
+  ouro_line spare;   /* virtualized list: retired segments (tag << 32 | chunk) */
+  unsigned long long hint[OURO_VL_HINTS];  /* virtualized list: segment lookaside */
+};
+
+struct ouro_glob {
+  ouro_line bump;        /* next never-carved chunk (may overshoot n_chunks) */
+  ouro_line pool_taken;  /* pool entries handed out (may overshoot pool_size) */
+  unsigned long long pool_size;
+  unsigned int error_bits;
+  unsigned int pad;
+};
+
+/* header of a virtualized-list segment (first 64 bytes of its chunk) */
+struct ouro_seg {
+  unsigned long long link;   /* (segment index << 32) | next chunk */
+  unsigned int done;         /* position events seen (2 per slot: produced, consumed) */
+  unsigned int spare_next;   /* next retired segment on the class spare stack */
+  unsigned long long pad[6];
+};
+
+namespace ouro {
+namespace detail {
+
+/* ------------------------------------------------------------ PTX helpers */
+__device__ __forceinline__ unsigned laneid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%laneid;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned smid() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned long long ld_acq(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_acq32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rlx(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rel(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long cas_rel(unsigned long long *p, unsigned long long c,
+                                                      unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.release.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(o) : "l"(p), "l"(c), "l"(v) : "memory");
+  return o;
+}
+__device__ __forceinline__ unsigned long long cas_ar(unsigned long long *p, unsigned long long c,
+                                                     unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.acq_rel.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(o) : "l"(p), "l"(c), "l"(v) : "memory");
+  return o;
+}
+
+/* ------------------------------------------------------------------ basics */
+__host__ __device__ __forceinline__ ouro_qhdr *qh(const ouro_heap_dev &h, int c) {
+  return reinterpret_cast<ouro_qhdr *>(h.qhdr) + c;
+}
+__device__ __forceinline__ ouro_glob *gl(const ouro_heap_dev &h) {
+  return reinterpret_cast<ouro_glob *>(h.glob);
+}
+__device__ __forceinline__ void stat_add(const ouro_heap_dev &h, int row, int kind,
+                                         unsigned long long v) {
+  if (v)
+    atomicAdd(&h.stats[((size_t)row * OURO_NSTAT + kind) * OURO_SHARDS + (smid() & (OURO_SHARDS - 1))], v);
+}
+__device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits) {
+  atomicOr(&gl(h)->error_bits, bits);
+}
+
+/* power-of-two class: ceil(log2 n) - 4, floor 16 B; -1 for 0 or above one chunk */
+__device__ __forceinline__ int size_class(const ouro_heap_dev &h, unsigned long long n) {
+  if (n == 0 || n > h.chunk_bytes) return -1;
+  if (n <= 16) return 0;
+  return 64 - __clzll(n - 1) - 4;
+}
+
+/* slot word: high 32 bits = sequence, low 32 bits = item.  For the slot of
+ * position p: seq p = empty, p+1 = item, p+2 = null answer (heap exhausted),
+ * >= p+3 = position retired (consumed; or given up by its consumer). */
+__device__ __forceinline__ unsigned long long slot(unsigned long long seq, unsigned item) {
+  return ((unsigned long long)(unsigned)seq << 32) | item;
+}
+__device__ __forceinline__ int slot_d(unsigned long long v, unsigned long long pos) {
+  return (int)((unsigned)(v >> 32) - (unsigned)pos);
+}
+
+__device__ __forceinline__ bool try_lock(unsigned long long *l) {
+  if (ld_rlx(l) != 0) return false;
+  return cas_ar(l, 0ull, 1ull) == 0ull;
+}
+__device__ __forceinline__ void unlock(unsigned long long *l) { st_rel(l, 0ull); }
+
+/* ------------------------------------------------------------ chunk supply */
+struct chunk_range {
+  unsigned long long p0, b0;
+  unsigned k1, k2;
+};
+/* Up to m chunks: pool entries first (in pool order), then never-carved
+ * chunks from the bump pointer. */
+__device__ inline chunk_range take_chunks(const ouro_heap_dev &h, unsigned m) {
+  chunk_range r{0, 0, 0, 0};
+  ouro_glob *g = gl(h);
+  const unsigned long long ps = ld_rlx(&g->pool_size);
+  if (m && ld_rlx(&g->pool_taken.v) < ps) {
+    unsigned long long pt = atomicAdd(&g->pool_taken.v, (unsigned long long)m);
+    if (pt < ps) {
+      r.p0 = pt;
+      r.k1 = (unsigned)min((unsigned long long)m, ps - pt);
+    }
+  }
+  unsigned rest = m - r.k1;
+  if (rest && ld_rlx(&g->bump.v) < h.n_chunks) {
+    unsigned long long b = atomicAdd(&g->bump.v, (unsigned long long)rest);
+    if (b < h.n_chunks) {
+      r.b0 = b;
+      r.k2 = (unsigned)min((unsigned long long)rest, h.n_chunks - b);
+    }
+  }
+  return r;
+}
+__device__ __forceinline__ unsigned range_chunk(const ouro_heap_dev &h, const chunk_range &r,
+                                                unsigned j) {
+  return j < r.k1 ? h.pool[r.p0 + j] : (unsigned)(r.b0 + (j - r.k1));
+}
+
+/* ------------------------------------------------------- array slot rings */
+__device__ __forceinline__ unsigned long long *ring_slot(const ouro_heap_dev &h, int c,
+                                                         unsigned long long pos) {
+  return h.cells + h.ring_off[c] + (pos & h.ring_mask[c]);
+}
+
+/* --------------------------------------------- virtualized-list segments */
+__device__ __forceinline__ ouro_seg *seg_of(const ouro_heap_dev &h, unsigned x) {
+  return reinterpret_cast<ouro_seg *>(h.base + ((size_t)x << h.log2_chunk));
+}
+__device__ __forceinline__ unsigned long long *seg_cells(const ouro_heap_dev &h, unsigned x) {
+  return reinterpret_cast<unsigned long long *>(h.base + ((size_t)x << h.log2_chunk) + OURO_SEG_HDR);
+}
+__device__ __forceinline__ unsigned hi32(unsigned long long v) { return (unsigned)(v >> 32); }
+__device__ __forceinline__ unsigned lo32(unsigned long long v) { return (unsigned)v; }
+__device__ __forceinline__ unsigned long long pack(unsigned a, unsigned b) {
+  return ((unsigned long long)a << 32) | b;
+}
+
+__device__ inline void spare_push(const ouro_heap_dev &h, int c, unsigned x) {
+  unsigned long long *top = &qh(h, c)->spare.v;
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    unsigned long long old = ld_acq(top);
+    seg_of(h, x)->spare_next = lo32(old);
+    __threadfence();
+    if (cas_ar(top, old, pack(hi32(old) + 1, x)) == old) return;
+  }
+  set_error(h, OURO_ERR_TIMEOUT);
+}
+__device__ inline unsigned spare_pop(const ouro_heap_dev &h, int c) {
+  unsigned long long *top = &qh(h, c)->spare.v;
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    unsigned long long old = ld_acq(top);
+    if (lo32(old) == OURO_NIL) return OURO_NIL;
+    unsigned nxt = *(volatile unsigned *)&seg_of(h, lo32(old))->spare_next;
+    if (cas_ar(top, old, pack(hi32(old) + 1, nxt)) == old) return lo32(old);
+  }
+  return OURO_NIL;
+}
+
+/* A fresh segment with index idx: spare of the class first, else a chunk of
+ * the heap.  Every slot starts empty for its own position. */
+__device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) {
+  unsigned x = spare_pop(h, c);
+  if (x == OURO_NIL) {
+    chunk_range r = take_chunks(h, 1);
+    if (r.k1 + r.k2 == 0) return OURO_NIL;
+    x = range_chunk(h, r, 0);
+    h.chunk_cls[x] = OURO_CLS_SEG;
+    stat_add(h, c, OURO_ST_SEG, 1);
+  }
+  ouro_seg *s = seg_of(h, x);
+  s->done = 0;
+  unsigned long long *cells = seg_cells(h, x);
+  const unsigned long long p0 = (unsigned long long)idx * h.seg_cap;
+  for (unsigned i = 0; i < h.seg_cap; i += 2) {
+    ulonglong2 v = make_ulonglong2(slot(p0 + i, 0), slot(p0 + i + 1, 0));
+    *reinterpret_cast<ulonglong2 *>(cells + i) = v;   /* seg_cap is even, cells 16-B aligned */
+  }
+  s->link = pack(idx, OURO_NIL);
+  __threadfence();
+  return x;
+}
+
+/* Retire fully used front segments (all slots produced and consumed, and a
+ * successor linked) onto the class spare stack. */
+__device__ inline void vl_advance(const ouro_heap_dev &h, int c) {
+  ouro_qhdr *q = qh(h, c);
+  for (int i = 0; i < 64; ++i) {
+    unsigned long long f = ld_acq(&q->front.v);
+    unsigned fx = lo32(f);
+    if (fx == OURO_NIL) return;
+    unsigned long long link = ld_acq(&seg_of(h, fx)->link);
+    if (hi32(link) != hi32(f)) continue;
+    unsigned nxt = lo32(link);
+    if (nxt == OURO_NIL) return;
+    if (ld_acq32(&seg_of(h, fx)->done) != 2u * h.seg_cap) return;
+    unsigned long long nf = pack(hi32(f) + 1, nxt);
+    cas_ar(&q->back.v, f, nf);           /* never leave the back hint on a retired segment */
+    if (cas_ar(&q->front.v, f, nf) == f) spare_push(h, c, fx);
+  }
+}
+
+/* n position events on the segment holding `cell` */
+__device__ inline void vl_event(const ouro_heap_dev &h, int c, const unsigned long long *cell,
+                                unsigned n) {
+  unsigned x = (unsigned)(((const unsigned char *)cell - h.base) >> h.log2_chunk);
+  unsigned r = atomicAdd(&seg_of(h, x)->done, n) + n;
+  if (r == 2u * h.seg_cap) {
+    __threadfence();
+    vl_advance(h, c);
+  }
+}
+
+/* Slot of position pos in the virtualized list of class c.  create: link
+ * missing segments (producers); otherwise null while the segment is not
+ * linked yet. */
+__device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                              bool create) {
+  ouro_qhdr *q = qh(h, c);
+  const unsigned long long s = pos / h.seg_cap;
+  const unsigned s32 = (unsigned)s;
+  const unsigned off = (unsigned)(pos - s * h.seg_cap);
+  unsigned long long e = ld_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)]);
+  if (hi32(e) == s32 && lo32(e) != OURO_NIL && hi32(ld_acq(&seg_of(h, lo32(e))->link)) == s32)
+    return seg_cells(h, lo32(e)) + off;
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    unsigned long long cur = ld_acq(&q->back.v);
+    if (lo32(cur) == OURO_NIL) {                     /* no segment yet */
+      if (!create) return nullptr;
+      unsigned x = seg_new(h, c, hi32(cur));
+      if (x == OURO_NIL) { set_error(h, OURO_ERR_QUEUE_FULL); return nullptr; }
+      unsigned long long nb = pack(hi32(cur), x);
+      if (cas_ar(&q->back.v, cur, nb) == cur) cas_ar(&q->front.v, cur, nb);
+      else spare_push(h, c, x);
+      continue;
+    }
+    if ((int)(s32 - hi32(cur)) < 0) {
+      cur = ld_acq(&q->front.v);
+      if (lo32(cur) == OURO_NIL || (int)(s32 - hi32(cur)) < 0) continue;
+    }
+    bool restart = false;
+    while (hi32(cur) != s32) {
+      unsigned cx = lo32(cur);
+      unsigned long long link = ld_acq(&seg_of(h, cx)->link);
+      if (hi32(link) != hi32(cur)) { restart = true; break; }   /* segment was recycled */
+      unsigned nxt = lo32(link);
+      if (nxt == OURO_NIL) {
+        if (!create) return nullptr;
+        unsigned x = seg_new(h, c, hi32(cur) + 1);
+        if (x == OURO_NIL) { set_error(h, OURO_ERR_QUEUE_FULL); return nullptr; }
+        unsigned long long old = cas_ar(&seg_of(h, cx)->link, link, pack(hi32(cur), x));
+        if (old == link) {
+          nxt = x;
+          cas_ar(&q->back.v, cur, pack(hi32(cur) + 1, x));
+          __threadfence();
+          vl_advance(h, c);
+        } else {
+          spare_push(h, c, x);
+          if (hi32(old) != hi32(cur)) { restart = true; break; }
+          nxt = lo32(old);
+        }
+      }
+      cur = pack(hi32(cur) + 1, nxt);
+    }
+    if (restart) continue;
+    st_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)], cur);
+    return seg_cells(h, lo32(cur)) + off;
+  }
+  set_error(h, OURO_ERR_TIMEOUT);
+  return nullptr;
+}
+
+/* slot of position pos for variant V (template-resolved) */
+template <bool VL>
+__device__ __forceinline__ unsigned long long *slot_at(const ouro_heap_dev &h, int c,
+                                                       unsigned long long pos, bool create) {
+  if (VL) return vl_slot(h, c, pos, create);
+  return ring_slot(h, c, pos);
+}
+
+/* ------------------------------------------------------- slot operations */
+/* Producer of position pos puts item (or the null marker).  0: placed;
+ * 1: the consumer gave the position up (caller re-queues the item);
+ * -1: an earlier lap never drained (timeout). */
+__device__ inline int put_at(const ouro_heap_dev &h, unsigned long long *cell, unsigned long long pos,
+                             unsigned item, bool null_marker) {
+  const unsigned long long want = null_marker ? slot(pos + 2, 0) : slot(pos + 1, item);
+  unsigned long long expect = slot(pos, 0);
+  unsigned ns = h.backoff_min_ns;
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    unsigned long long old = cas_rel(cell, expect, want);
+    if (old == expect) return 0;
+    int d = slot_d(old, pos);
+    if (d == 0) { expect = old; continue; }   /* empty slot with a posted value */
+    if (d >= 3) return 1;
+    __nanosleep(ns);
+    ns = min(ns * 2, h.backoff_max_ns);
+    expect = slot(pos, 0);
+  }
+  set_error(h, OURO_ERR_QUEUE_OVERFLOW);
+  return -1;
+}
+
+/* Consumer of position pos: 1 item, 2 null marker, 0 not there yet.
+ * retired_seq: what the slot becomes (array rings: pos + ring size, ready
+ * for the producer of the next lap; lists leave single-use slots alone). */
+template <bool VL>
+__device__ __forceinline__ int try_take(const ouro_heap_dev &h, int c, unsigned long long *cell,
+                                        unsigned long long pos, unsigned *item) {
+  unsigned long long v = ld_acq(cell);
+  int d = slot_d(v, pos);
+  if (d == 1 || d == 2) {
+    *item = lo32(v);
+    if (!VL) st_rlx(cell, slot(pos + h.ring_mask[c] + 1, 0));
+    return d;
+  }
+  return 0;
+}
+
+/* Consumer gives up position pos: 3 given up, 1/2 the answer arrived
+ * meanwhile, 0 not possible now (an earlier lap still holds the slot). */
+template <bool VL>
+__device__ inline int give_up(const ouro_heap_dev &h, int c, unsigned long long *cell,
+                              unsigned long long pos, unsigned *item) {
+  const unsigned long long retired = VL ? slot(pos + 3, 0) : slot(pos + h.ring_mask[c] + 1, 0);
+  for (int it = 0; it < 8; ++it) {
+    unsigned long long v = ld_acq(cell);
+    int d = slot_d(v, pos);
+    if (d == 1 || d == 2) {
+      *item = lo32(v);
+      if (!VL) st_rlx(cell, retired);
+      return d;
+    }
+    if (d != 0) return 0;
+    if (cas_ar(cell, v, retired) == v) return 3;
+  }
+  return 0;
+}
+
+/* Queue one item at a fresh producer position (re-queue after a give-up). */
+template <bool VL>
+__device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
+  ouro_qhdr *q = qh(h, c);
+  for (int tries = 0; tries < 64; ++tries) {
+    unsigned long long t = atomicAdd(&q->tail.v, 1ull);
+    unsigned long long *cell = slot_at<VL>(h, c, t, true);
+    if (!cell) return;   /* error already recorded */
+    int rc = put_at(h, cell, t, item, false);
+    if (VL) vl_event(h, c, cell, 1);
+    if (rc == 0) return;
+    if (rc < 0) return;
+    stat_add(h, c, OURO_ST_REPUSH, 1);
+  }
+  set_error(h, OURO_ERR_TIMEOUT);
+}
+
+/* ---------------------------------------------- page queues: carve batch */
+/* Called by every lane of vmask; lane `owner` holds the carve lock of class
+ * c and releases it.  Carves the chunks the class's current debt needs (one
+ * batch), then the warp writes the new page ids into the debt slots.  If the
+ * heap (or the page-array capacity) is exhausted, the remaining debt slots
+ * get the null marker. */
+template <int V>
+__device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
+  constexpr bool VL = (V == OURO_PAGE_VLIST);
+  ouro_qhdr *q = qh(h, c);
+  const unsigned lane = laneid();
+  const unsigned ppc_log = h.log2_chunk - 4 - c;
+  const unsigned long long ppc = 1ull << ppc_log;
+  unsigned m = 0;
+  int exhausted = 0;
+  unsigned long long t0 = 0;
+  chunk_range r{0, 0, 0, 0};
+  if ((int)lane == owner) {
+    unsigned long long t = ld_acq(&q->tail.v), hd = ld_acq(&q->head.v);
+    if (hd > t) {
+      unsigned long long want = (hd - t + ppc - 1) >> ppc_log;
+      unsigned long long ask = min(want, (unsigned long long)h.max_carve);
+      if (V == OURO_PAGE_ARRAY) {
+        unsigned long long limit = h.qcap[c] >> ppc_log, have = ld_rlx(&q->carved.v);
+        ask = have >= limit ? 0 : min(ask, limit - have);
+      }
+      if (VL) {
+        /* queue storage first: segments for every slot this carve (or its
+         * null answers) will write, before the data chunks are taken */
+        unsigned long long last = max(hd, t + (ask << ppc_log)) - 1;
+        vl_slot(h, c, last, true);
+      }
+      if (ask) r = take_chunks(h, (unsigned)ask);
+      m = r.k1 + r.k2;
+      exhausted = m < ask || ask == 0;
+      if (m) {
+        t0 = atomicAdd(&q->tail.v, (unsigned long long)m << ppc_log);
+        atomicAdd(&q->carved.v, (unsigned long long)m);
+        stat_add(h, c, OURO_ST_CARVE, m);
+      }
+    }
+  }
+  m = __shfl_sync(vmask, m, owner);
+  exhausted = __shfl_sync(vmask, exhausted, owner);
+  t0 = __shfl_sync(vmask, t0, owner);
+  r.p0 = __shfl_sync(vmask, r.p0, owner);
+  r.b0 = __shfl_sync(vmask, r.b0, owner);
+  r.k1 = __shfl_sync(vmask, r.k1, owner);
+  r.k2 = __shfl_sync(vmask, r.k2, owner);
+  const unsigned nl = __popc(vmask), rk = __popc(vmask & lanemask_lt());
+  if (m) {
+    for (unsigned i = rk; i < m; i += nl) h.chunk_cls[range_chunk(h, r, i)] = (unsigned char)c;
+    if (h.checked)
+      for (unsigned long long i = rk; i < ((unsigned long long)m << ppc_log); i += nl) {
+        unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
+        unsigned pg = (unsigned)(i & (ppc - 1));
+        atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], 1u << (pg & 31));
+      }
+    __threadfence();
+    __syncwarp(vmask);
+    const unsigned long long total = (unsigned long long)m << ppc_log;
+    for (unsigned long long i = rk; i < total; i += nl) {
+      unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
+      unsigned item = (x << ppc_log) | (unsigned)(i & (ppc - 1));
+      unsigned long long p = t0 + i;
+      unsigned long long *cell = slot_at<VL>(h, c, p, true);
+      if (!cell) continue;   /* queue storage exhausted: recorded */
+      int rc = put_at(h, cell, p, item, false);
+      if (VL) vl_event(h, c, cell, 1);
+      if (rc == 1) push_one<VL>(h, c, item);
+    }
+  }
+  if (exhausted) {
+    unsigned long long dt = 0, dn = 0;
+    if ((int)lane == owner) {
+      for (unsigned it = 0; it < h.spin_limit; ++it) {
+        unsigned long long t = ld_acq(&q->tail.v), hd = ld_acq(&q->head.v);
+        if (hd <= t) break;
+        if (atomicCAS(&q->tail.v, t, hd) == t) { dt = t; dn = hd - t; break; }
+      }
+      stat_add(h, c, OURO_ST_DEAD, dn);
+    }
+    dt = __shfl_sync(vmask, dt, owner);
+    dn = __shfl_sync(vmask, dn, owner);
+    for (unsigned long long i = rk; i < dn; i += nl) {
+      unsigned long long p = dt + i;
+      unsigned long long *cell = slot_at<VL>(h, c, p, true);
+      if (!cell) continue;
+      put_at(h, cell, p, 0, true);
+      if (VL) vl_event(h, c, cell, 1);
+    }
+  }
+  __syncwarp(vmask);
+  if ((int)lane == owner) unlock(&q->lock.v);
+}
+
+/* --------------------------------------------------------- page queues */
+/* All lanes of vmask hold a request of class cls (any mix of classes). */
+template <int V>
+__device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
+  constexpr bool VL = (V == OURO_PAGE_VLIST);
+  ouro_qhdr *q = qh(h, cls);
+  const unsigned lane = laneid();
+  const unsigned grp = __match_any_sync(vmask, cls);
+  const unsigned leader = __ffs(grp) - 1;
+  const unsigned rank = __popc(grp & lanemask_lt());
+  unsigned long long pos = 0;
+  if (lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
+  pos = __shfl_sync(vmask, pos, leader) + rank;
+
+  unsigned item = 0;
+  int st = 0;   /* 0 waiting, 1 item, 2 null answer, 3 gave up */
+  unsigned long long *cell = slot_at<VL>(h, cls, pos, false);
+  if (cell) st = try_take<VL>(h, cls, cell, pos, &item);
+
+  if (__ballot_sync(vmask, st == 0)) {
+    unsigned ns = h.backoff_min_ns;
+    for (unsigned it = 0;; ++it) {
+      bool debt = false, progressed = false;
+      if (st == 0) {
+        if (VL && !cell) cell = vl_slot(h, cls, pos, false);
+        if (cell) st = try_take<VL>(h, cls, cell, pos, &item);
+        if (st) progressed = true;
+        else debt = pos >= ld_acq(&q->tail.v);
+      }
+      const unsigned dmask = __ballot_sync(vmask, debt);
+      if (dmask) {
+        const unsigned same = __match_any_sync(vmask, debt ? cls : -1);
+        const bool trier = debt && lane == (unsigned)(__ffs(same) - 1);
+        const bool got = trier && try_lock(&q->lock.v);
+        unsigned lockers = __ballot_sync(vmask, got);
+        while (lockers) {
+          const int j = __ffs(lockers) - 1;
+          lockers &= lockers - 1;
+          page_carve<V>(h, __shfl_sync(vmask, cls, j), vmask, j);
+        }
+      }
+      const unsigned waiting = __ballot_sync(vmask, st == 0);
+      if (!waiting) break;
+      if (it >= h.spin_limit) {
+        if (st == 0) {   /* give the position up so its producer re-queues the item */
+          if (!cell) cell = slot_at<VL>(h, cls, pos, true);
+          int g = cell ? give_up<VL>(h, cls, cell, pos, &item) : 0;
+          st = g ? g : 3;
+          if (st == 3) {
+            set_error(h, OURO_ERR_TIMEOUT);
+            stat_add(h, cls, OURO_ST_CANCEL, 1);
+          }
+        }
+        break;
+      }
+      if (!__any_sync(vmask, progressed)) {
+        __nanosleep(ns);
+        ns = min(ns * 2, h.backoff_max_ns);
+      } else {
+        ns = h.backoff_min_ns;
+      }
+    }
+  }
+  if (VL && cell && st != 0) vl_event(h, cls, cell, 1);
+
+  void *res = nullptr;
+  if (st == 1) {
+    if (h.checked) {
+      unsigned pg = item & ((1u << (h.log2_chunk - 4 - cls)) - 1);
+      unsigned x = item >> (h.log2_chunk - 4 - cls);
+      unsigned bit = 1u << (pg & 31);
+      unsigned old = atomicAnd(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], ~bit);
+      if (!(old & bit)) set_error(h, OURO_ERR_DOUBLE_FREE);
+    }
+    res = h.base + ((size_t)item << (4 + cls));
+  }
+  /* per-class counters, one update per class group of the warp */
+  const unsigned g2 = __match_any_sync(vmask, cls);
+  const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
+  if (lane == (unsigned)(__ffs(g2) - 1)) {
+    stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
+    stat_add(h, cls, OURO_ST_FAILED, __popc(g2) - __popc(okm));
+  }
+  return res;
+}
+
+template <int V>
+__device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsigned vmask) {
+  constexpr bool VL = (V == OURO_PAGE_VLIST);
+  ouro_qhdr *q = qh(h, cls);
+  const unsigned lane = laneid();
+  const unsigned grp = __match_any_sync(vmask, cls);
+  const unsigned leader = __ffs(grp) - 1;
+  const unsigned rank = __popc(grp & lanemask_lt());
+  unsigned long long t = 0;
+  if (lane == leader) {
+    t = atomicAdd(&q->tail.v, (unsigned long long)__popc(grp));
+    stat_add(h, cls, OURO_ST_FREE, __popc(grp));
+  }
+  t = __shfl_sync(vmask, t, leader) + rank;
+  unsigned long long *cell = slot_at<VL>(h, cls, t, true);
+  if (!cell) return;   /* queue storage exhausted (recorded): the page is lost */
+  int rc = put_at(h, cell, t, item, false);
+  if (VL) vl_event(h, cls, cell, 1);
+  if (rc == 1) {
+    stat_add(h, cls, OURO_ST_REPUSH, 1);
+    push_one<VL>(h, cls, item);
+  }
+}
+
+/* Locate a block: class and page id, or -1 after recording a bad free. */
+__device__ __forceinline__ int locate(const ouro_heap_dev &h, const void *p, unsigned *item) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  if (b < h.base || b >= h.base + h.bytes) return -1;
+  const unsigned long long off = (unsigned long long)(b - h.base);
+  const unsigned c = h.chunk_cls[off >> h.log2_chunk];
+  if (c >= h.n_classes) return -1;
+  if (off & ((16ull << c) - 1)) return -1;
+  *item = (unsigned)(off >> (4 + c));
+  return (int)c;
+}
+
+}  // namespace detail
+}  // namespace ouro
+
+/* ------------------------------------------------------------- public API */
+/* Allocate n bytes from the heap; null when n is 0 or above one chunk, when
+ * the heap is exhausted, or when a bounded wait ran out. */
+static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t n) {
+  using namespace ouro::detail;
+  const unsigned mask = __activemask();
+  const int cls = size_class(h, n);
+  const unsigned vmask = __ballot_sync(mask, cls >= 0);
+  if (cls < 0) {
+    stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+    return nullptr;
+  }
+  switch (h.variant) {
+    case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, vmask);
+    case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, vmask);
+    default: return nullptr;
+  }
+}
+
+/* Return a block to the heap; null is ignored; a pointer that is not a live
+ * block start sets OURO_ERR_BAD_FREE (or OURO_ERR_DOUBLE_FREE) and is ignored. */
+static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
+  using namespace ouro::detail;
+  const unsigned mask = __activemask();
+  unsigned item = 0;
+  int cls = -1;
+  if (p) {
+    cls = locate(h, p, &item);
+    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE);
+    else if (h.checked) {
+      unsigned ppcm = (1u << (h.log2_chunk - 4 - cls)) - 1;
+      unsigned pg = item & ppcm, x = item >> (h.log2_chunk - 4 - cls);
+      unsigned bit = 1u << (pg & 31);
+      __threadfence();
+      unsigned old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bit);
+      if (old & bit) { set_error(h, OURO_ERR_DOUBLE_FREE); cls = -1; }
+    }
+  }
+  const unsigned vmask = __ballot_sync(mask, cls >= 0);
+  if (cls < 0) return;
+  switch (h.variant) {
+    case OURO_PAGE_ARRAY: page_free<OURO_PAGE_ARRAY>(h, cls, item, vmask); break;
+    case OURO_PAGE_VLIST: page_free<OURO_PAGE_VLIST>(h, cls, item, vmask); break;
+    default: break;
+  }
+}
+
+#endif

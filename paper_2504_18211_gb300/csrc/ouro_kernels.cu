@@ -1,0 +1,354 @@
+/*
+ * Batch API and driver-round kernels.
+ *
+ * The paper's driver (Sec. 3 of arXiv 2504.18211) allocates, writes some
+ * data, reads it back to check it, and frees, ten times over.  Two forms:
+ *   - per launch: ouro_batch_malloc, ouro_pattern_write, ouro_pattern_check,
+ *     ouro_batch_free (four kernels per round);
+ *   - fused: ouro_round_fused, one kernel per round; the allocator state
+ *     stays in L2 while every warp streams its own blocks.
+ * Payload traffic is warp-cooperative: the 32 blocks of a warp are cut into
+ * 16-byte units that the 32 lanes write and read in turn, so stores and
+ * loads are 16-byte vectors that coalesce within each block.
+ */
+#include "ouro_internal.cuh"
+
+using namespace ouro::detail;
+
+namespace {
+
+template <int V>
+__device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long long n) {
+  const unsigned mask = __activemask();
+  const int cls = size_class(h, n);
+  const unsigned vmask = __ballot_sync(mask, cls >= 0);
+  if (cls < 0) {
+    stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+    return nullptr;
+  }
+  return page_malloc<V>(h, cls, vmask);
+}
+
+template <int V>
+__device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
+  const unsigned mask = __activemask();
+  unsigned item = 0;
+  int cls = -1;
+  if (p) {
+    cls = locate(h, p, &item);
+    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE);
+    else if (h.checked) {
+      const unsigned sh = h.log2_chunk - 4 - cls;
+      const unsigned pg = item & ((1u << sh) - 1), x = item >> sh, bit = 1u << (pg & 31);
+      __threadfence();
+      unsigned old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bit);
+      if (old & bit) {
+        set_error(h, OURO_ERR_DOUBLE_FREE);
+        cls = -1;
+      }
+    }
+  }
+  const unsigned vmask = __ballot_sync(mask, cls >= 0);
+  if (cls < 0) return;
+  page_free<V>(h, cls, item, vmask);
+}
+
+/* ------------------------------------------------------------ batch API */
+template <int V>
+__global__ void k_batch_malloc(ouro_heap_dev h, const uint32_t *sizes, void **ptrs, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    ptrs[i] = malloc_v<V>(h, sizes[i]);
+}
+
+template <int V>
+__global__ void k_batch_free(ouro_heap_dev h, void *const *ptrs, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    free_v<V>(h, ptrs[i]);
+}
+
+/* ------------------------------------------------------------- payload */
+/* MurmurHash3 32-bit finalizer (Appleby, public domain) */
+__device__ __forceinline__ uint32_t fmix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return x;
+}
+#define OURO_GOLD 0x9E3779B9u
+
+struct acc {
+  unsigned long long mism = 0, x = 0, s = 0, words = 0;
+  __device__ void fold(uint32_t v) {
+    x ^= v;
+    s += v;
+    words++;
+  }
+};
+
+/* Warp-cooperative payload over the 32 blocks of a warp.  Every lane of the
+ * warp must call (a lane without a block passes p = null).  write: store
+ * the pattern; check: read back, compare, fold checksums into a.
+ * mode 0: word 0 = tid.  mode 1: floor(size/4) words key + w*GOLD, then the
+ * low size%4 bytes of word floor(size/4). */
+template <bool WRITE>
+__device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint32_t seed, int mode,
+                             acc &a) {
+  const unsigned lane = laneid();
+  if (mode == 0) {
+    if (p) {
+      if (WRITE) *reinterpret_cast<uint32_t *>(p) = tid;
+      else {
+        uint32_t v = *reinterpret_cast<const uint32_t *>(p);
+        a.mism += v != tid;
+        a.fold(v);
+      }
+    }
+    return;
+  }
+  const uint32_t key = fmix32(seed ^ (tid * OURO_GOLD));
+  const uint32_t units = p ? (size + 15) >> 4 : 0;
+  /* inclusive prefix of units over the warp */
+  uint32_t incl = units;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  for (uint32_t u0 = 0; u0 < total; u0 += 32) {
+    const uint32_t u = u0 + lane;
+    /* block j = number of lanes whose inclusive prefix is <= u */
+    int j = 0;
+    for (int step = 16; step; step >>= 1) {
+      uint32_t pv = __shfl_sync(0xffffffffu, incl, j + step - 1);
+      if (u < total && pv <= u) j += step;
+    }
+    const uint32_t before = j ? __shfl_sync(0xffffffffu, incl, (j - 1) & 31) : 0;
+    unsigned long long bp = __shfl_sync(0xffffffffu, (unsigned long long)p, j & 31);
+    uint32_t bsize = __shfl_sync(0xffffffffu, size, j & 31);
+    uint32_t bkey = __shfl_sync(0xffffffffu, key, j & 31);
+    if (u >= total) continue;
+    const uint32_t k = u - (j ? before : 0);    /* unit inside block j */
+    unsigned char *base = reinterpret_cast<unsigned char *>(bp) + 16ull * k;
+    const uint32_t w0 = 4 * k, nw = bsize >> 2, tail = bsize & 3;
+    if (w0 + 4 <= nw) {
+      uint4 want = make_uint4(bkey + w0 * OURO_GOLD, bkey + (w0 + 1) * OURO_GOLD,
+                              bkey + (w0 + 2) * OURO_GOLD, bkey + (w0 + 3) * OURO_GOLD);
+      if (WRITE) {
+        *reinterpret_cast<uint4 *>(base) = want;
+      } else {
+        uint4 got = *reinterpret_cast<const uint4 *>(base);
+        a.mism += (got.x != want.x) + (got.y != want.y) + (got.z != want.z) + (got.w != want.w);
+        a.fold(got.x);
+        a.fold(got.y);
+        a.fold(got.z);
+        a.fold(got.w);
+      }
+    } else {
+      uint32_t *wp = reinterpret_cast<uint32_t *>(base);
+      for (uint32_t w = w0; w < nw && w < w0 + 4; ++w) {
+        const uint32_t want = bkey + w * OURO_GOLD;
+        if (WRITE) wp[w - w0] = want;
+        else {
+          uint32_t got = wp[w - w0];
+          a.mism += got != want;
+          a.fold(got);
+        }
+      }
+      if (tail && nw < w0 + 4) {
+        const uint32_t v = bkey + nw * OURO_GOLD;
+        unsigned char *tb = reinterpret_cast<unsigned char *>(bp) + 4ull * nw;
+        if (WRITE) {
+          for (uint32_t b = 0; b < tail; ++b) tb[b] = (unsigned char)(v >> (8 * b));
+        } else {
+          uint32_t got = 0;
+          for (uint32_t b = 0; b < tail; ++b) {
+            unsigned char gb = tb[b];
+            a.mism += gb != (unsigned char)(v >> (8 * b));
+            got |= (uint32_t)gb << (8 * b);
+          }
+          a.fold(got);
+        }
+      }
+    }
+  }
+}
+
+/* block reduction of the check counters into *out */
+__device__ void flush_acc(acc &a, unsigned long long nulls, ouro_check *out) {
+  __shared__ unsigned long long sm[5];
+  if (threadIdx.x < 5) sm[threadIdx.x] = 0;
+  __syncthreads();
+  for (int o = 16; o; o >>= 1) {
+    a.mism += __shfl_xor_sync(0xffffffffu, a.mism, o);
+    a.x ^= __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.s += __shfl_xor_sync(0xffffffffu, a.s, o);
+    a.words += __shfl_xor_sync(0xffffffffu, a.words, o);
+    nulls += __shfl_xor_sync(0xffffffffu, nulls, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sm[0], nulls);
+    atomicAdd(&sm[1], a.mism);
+    atomicXor(&sm[2], a.x);
+    atomicAdd(&sm[3], a.s);
+    atomicAdd(&sm[4], a.words);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (sm[0]) atomicAdd(&out->nulls, sm[0]);
+    if (sm[1]) atomicAdd(&out->mismatches, sm[1]);
+    atomicXor(&out->xor64, sm[2]);
+    atomicAdd(&out->sum64, sm[3]);
+    atomicAdd(&out->words, sm[4]);
+  }
+}
+
+template <bool WRITE>
+__global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, uint32_t seed, int mode,
+                          ouro_check *out) {
+  acc a;
+  unsigned long long nulls = 0;
+  const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  const size_t wid = (((size_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5;
+  for (size_t base = wid * 32; base < n; base += warps * 32) {
+    const size_t i = base + (threadIdx.x & 31);
+    unsigned char *p = i < n ? static_cast<unsigned char *>(ptrs[i]) : nullptr;
+    const uint32_t sz = i < n ? sizes[i] : 0;
+    if (i < n && !p) nulls++;
+    warp_payload<WRITE>(p, sz, (uint32_t)i, seed, mode, a);
+  }
+  if (!WRITE) flush_acc(a, nulls, out);
+}
+
+/* one whole round per thread: malloc, write, read back, free */
+template <int V>
+__global__ void __launch_bounds__(256) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
+                                                     uint32_t seed, int mode, ouro_check *out, void **ptrs) {
+  acc a;
+  unsigned long long nulls = 0;
+  const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  const size_t wid = (((size_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5;
+  for (size_t base = wid * 32; base < n; base += warps * 32) {
+    const size_t i = base + (threadIdx.x & 31);
+    const uint32_t sz = i < n ? sizes[i] : 0;
+    unsigned char *p = nullptr;
+    if (i < n) {
+      p = static_cast<unsigned char *>(malloc_v<V>(h, sz));
+      if (!p) nulls++;
+      if (ptrs) ptrs[i] = p;
+    }
+    __syncwarp();
+    warp_payload<true>(p, sz, (uint32_t)i, seed, mode, a);
+    __syncwarp();
+    warp_payload<false>(p, sz, (uint32_t)i, seed, mode, a);
+    __syncwarp();
+    if (i < n) free_v<V>(h, p);
+    __syncwarp();
+  }
+  flush_acc(a, nulls, out);
+}
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename K>
+int occupancy_grid(K kernel, int block) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * ouro::host::sm_count();
+}
+
+inline int grid_for(size_t n, int block, int cap) {
+  size_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  return (int)(g < (size_t)cap ? g : (size_t)cap);
+}
+
+}  // namespace
+
+/* ------------------------------------------------------------- C entries */
+extern "C" ouro_status ouro_batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n,
+                                         void *stream) {
+  if (!H || (n && (!d_sizes || !d_ptrs))) return OURO_EINVAL;
+  if (!n) return OURO_OK;
+  const int block = 256;
+  switch (H->d.variant) {
+    case OURO_PAGE_ARRAY: {
+      int g = grid_for(n, block, 1 << 20);
+      k_batch_malloc<OURO_PAGE_ARRAY><<<g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n);
+      break;
+    }
+    case OURO_PAGE_VLIST: {
+      int g = grid_for(n, block, 1 << 20);
+      k_batch_malloc<OURO_PAGE_VLIST><<<g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n);
+      break;
+    }
+    default: return OURO_ENOTSUP;
+  }
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, void *stream) {
+  if (!H || (n && !d_ptrs)) return OURO_EINVAL;
+  if (!n) return OURO_OK;
+  const int block = 256;
+  const int g = grid_for(n, block, 1 << 20);
+  switch (H->d.variant) {
+    case OURO_PAGE_ARRAY: k_batch_free<OURO_PAGE_ARRAY><<<g, block, 0, S(stream)>>>(H->d, d_ptrs, n); break;
+    case OURO_PAGE_VLIST: k_batch_free<OURO_PAGE_VLIST><<<g, block, 0, S(stream)>>>(H->d, d_ptrs, n); break;
+    default: return OURO_ENOTSUP;
+  }
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_pattern_write(void *const *d_ptrs, const uint32_t *d_sizes, size_t n, uint32_t seed,
+                                          int mode, void *stream) {
+  if (n && (!d_ptrs || !d_sizes)) return OURO_EINVAL;
+  if (mode != 0 && mode != 1) return OURO_EINVAL;
+  if (!n) return OURO_OK;
+  const int block = 256;
+  const int g = grid_for((n + 31) / 32 * 32, block, occupancy_grid(k_pattern<true>, block));
+  k_pattern<true><<<g, block, 0, S(stream)>>>(d_ptrs, d_sizes, n, seed, mode, nullptr);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_pattern_check(void *const *d_ptrs, const uint32_t *d_sizes, size_t n, uint32_t seed,
+                                          int mode, ouro_check *d_out, void *stream) {
+  if (!d_out || (n && (!d_ptrs || !d_sizes))) return OURO_EINVAL;
+  if (mode != 0 && mode != 1) return OURO_EINVAL;
+  OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
+  if (!n) return OURO_OK;
+  const int block = 256;
+  const int g = grid_for((n + 31) / 32 * 32, block, occupancy_grid(k_pattern<false>, block));
+  k_pattern<false><<<g, block, 0, S(stream)>>>(d_ptrs, d_sizes, n, seed, mode, d_out);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_round_fused(ouro_heap *H, const uint32_t *d_sizes, size_t n, uint32_t seed, int mode,
+                                        ouro_check *d_out, void **d_ptrs, void *stream) {
+  if (!H || !d_out || (n && !d_sizes)) return OURO_EINVAL;
+  if (mode != 0 && mode != 1) return OURO_EINVAL;
+  OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
+  if (!n) return OURO_OK;
+  const int block = 256;
+  switch (H->d.variant) {
+    case OURO_PAGE_ARRAY: {
+      int g = grid_for(n, block, occupancy_grid(k_round_fused<OURO_PAGE_ARRAY>, block));
+      k_round_fused<OURO_PAGE_ARRAY><<<g, block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs);
+      break;
+    }
+    case OURO_PAGE_VLIST: {
+      int g = grid_for(n, block, occupancy_grid(k_round_fused<OURO_PAGE_VLIST>, block));
+      k_round_fused<OURO_PAGE_VLIST><<<g, block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs);
+      break;
+    }
+    default: return OURO_ENOTSUP;
+  }
+  OURO_LAUNCHED();
+  return OURO_OK;
+}

@@ -1,0 +1,35 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle.
+
+Pure input generation: numpy PCG64 streams, no allocator arithmetic.  Seeds
+default to 0x0A110C00 + workload index.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 0x0A110C00
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def small_sizes(threads: int = 40 * 256, size: int = 16) -> np.ndarray:
+    """Plain-method small run: every thread asks for the same size."""
+    return np.full(threads, size, dtype=np.uint32)
+
+
+def sweep_sizes(threads: int = 1 << 20, seed: int = SEED_BASE + 1, kmin: int = 4,
+                kmax: int = 13) -> np.ndarray:
+    """Size sweep: each thread asks for 2**k bytes, k uniform in [kmin, kmax]."""
+    k = rng(seed).integers(kmin, kmax + 1, size=threads)
+    return (np.uint32(1) << k.astype(np.uint32)).astype(np.uint32)
+
+
+def uniform_sizes(threads: int, lo: int = 4, hi: int = 8192, seed: int = SEED_BASE + 3) -> np.ndarray:
+    """Sizes uniform over the integers [lo, hi]."""
+    return rng(seed).integers(lo, hi + 1, size=threads).astype(np.uint32)
+
+
+def single_size(threads: int, size: int) -> np.ndarray:
+    return np.full(threads, size, dtype=np.uint32)
