@@ -40,6 +40,7 @@
 #include "ouro.h"
 
 #define OURO_NIL 0xFFFFFFFFu
+#define OURO_BUSY 0xFFFFFFFEu   /* successor segment being created by one thread */
 #define OURO_CLS_NONE 0xFFu
 #define OURO_CLS_SEG 0xFEu
 #define OURO_VL_HINTS 64
@@ -285,11 +286,11 @@ __device__ inline void vl_advance(const ouro_heap_dev &h, int c) {
   for (int i = 0; i < 64; ++i) {
     unsigned long long f = ld_acq(&q->front.v);
     unsigned fx = lo32(f);
-    if (fx == OURO_NIL) return;
+    if (fx >= OURO_BUSY) return;
     unsigned long long link = ld_acq(&seg_of(h, fx)->link);
     if (hi32(link) != hi32(f)) continue;
     unsigned nxt = lo32(link);
-    if (nxt == OURO_NIL) return;
+    if (nxt >= OURO_BUSY) return;
     if (ld_acq32(&seg_of(h, fx)->done) != 2u * h.seg_cap) return;
     unsigned long long nf = pack(hi32(f) + 1, nxt);
     cas_ar(&q->back.v, f, nf);           /* never leave the back hint on a retired segment */
@@ -310,7 +311,8 @@ __device__ inline void vl_event(const ouro_heap_dev &h, int c, const unsigned lo
 
 /* Slot of position pos in the virtualized list of class c.  create: link
  * missing segments (producers); otherwise null while the segment is not
- * linked yet. */
+ * linked yet.  One thread creates each segment: it first claims the empty
+ * link (next = OURO_BUSY); others wait for the link instead of creating. */
 __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
                                               bool create) {
   ouro_qhdr *q = qh(h, c);
@@ -318,50 +320,72 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
   const unsigned s32 = (unsigned)s;
   const unsigned off = (unsigned)(pos - s * h.seg_cap);
   unsigned long long e = ld_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)]);
-  if (hi32(e) == s32 && lo32(e) != OURO_NIL && hi32(ld_acq(&seg_of(h, lo32(e))->link)) == s32)
+  if (hi32(e) == s32 && lo32(e) < OURO_BUSY && hi32(ld_acq(&seg_of(h, lo32(e))->link)) == s32)
     return seg_cells(h, lo32(e)) + off;
+  unsigned ns = h.backoff_min_ns;
+  unsigned long long cur = 0;
+  bool walking = false;
   for (unsigned it = 0; it < h.spin_limit; ++it) {
-    unsigned long long cur = ld_acq(&q->back.v);
-    if (lo32(cur) == OURO_NIL) {                     /* no segment yet */
+    if (!walking) {
+      cur = ld_acq(&q->back.v);
+      if (lo32(cur) == OURO_NIL) {                   /* no segment yet: claim the first */
+        if (!create) return nullptr;
+        const unsigned long long busy = pack(hi32(cur), OURO_BUSY);
+        if (cas_ar(&q->back.v, cur, busy) == cur) {
+          unsigned x = seg_new(h, c, hi32(cur));
+          if (x == OURO_NIL) {
+            st_rel(&q->back.v, cur);
+            set_error(h, OURO_ERR_QUEUE_FULL);
+            return nullptr;
+          }
+          st_rel(&q->front.v, pack(hi32(cur), x));
+          st_rel(&q->back.v, pack(hi32(cur), x));
+        }
+        continue;
+      }
+      if (lo32(cur) == OURO_BUSY) {                  /* first segment being created */
+        __nanosleep(ns);
+        ns = min(ns * 2, h.backoff_max_ns);
+        continue;
+      }
+      if ((int)(s32 - hi32(cur)) < 0) {
+        cur = ld_acq(&q->front.v);
+        if (lo32(cur) >= OURO_BUSY || (int)(s32 - hi32(cur)) < 0) continue;
+      }
+      walking = true;
+    }
+    if (hi32(cur) == s32) {
+      st_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)], cur);
+      return seg_cells(h, lo32(cur)) + off;
+    }
+    ouro_seg *sg = seg_of(h, lo32(cur));
+    const unsigned long long link = ld_acq(&sg->link);
+    if (hi32(link) != hi32(cur)) { walking = false; continue; }   /* segment was recycled */
+    const unsigned nxt = lo32(link);
+    if (nxt == OURO_NIL) {
       if (!create) return nullptr;
-      unsigned x = seg_new(h, c, hi32(cur));
-      if (x == OURO_NIL) { set_error(h, OURO_ERR_QUEUE_FULL); return nullptr; }
-      unsigned long long nb = pack(hi32(cur), x);
-      if (cas_ar(&q->back.v, cur, nb) == cur) cas_ar(&q->front.v, cur, nb);
-      else spare_push(h, c, x);
+      if (cas_ar(&sg->link, link, pack(hi32(cur), OURO_BUSY)) == link) {
+        unsigned x = seg_new(h, c, hi32(cur) + 1);
+        if (x == OURO_NIL) {
+          st_rel(&sg->link, link);
+          set_error(h, OURO_ERR_QUEUE_FULL);
+          return nullptr;
+        }
+        st_rel(&sg->link, pack(hi32(cur), x));
+        const unsigned long long nb = pack(hi32(cur) + 1, x);
+        cas_ar(&q->back.v, cur, nb);
+        __threadfence();
+        vl_advance(h, c);
+        cur = nb;
+      }
       continue;
     }
-    if ((int)(s32 - hi32(cur)) < 0) {
-      cur = ld_acq(&q->front.v);
-      if (lo32(cur) == OURO_NIL || (int)(s32 - hi32(cur)) < 0) continue;
+    if (nxt == OURO_BUSY) {                          /* someone is creating the successor */
+      __nanosleep(ns);
+      ns = min(ns * 2, h.backoff_max_ns);
+      continue;
     }
-    bool restart = false;
-    while (hi32(cur) != s32) {
-      unsigned cx = lo32(cur);
-      unsigned long long link = ld_acq(&seg_of(h, cx)->link);
-      if (hi32(link) != hi32(cur)) { restart = true; break; }   /* segment was recycled */
-      unsigned nxt = lo32(link);
-      if (nxt == OURO_NIL) {
-        if (!create) return nullptr;
-        unsigned x = seg_new(h, c, hi32(cur) + 1);
-        if (x == OURO_NIL) { set_error(h, OURO_ERR_QUEUE_FULL); return nullptr; }
-        unsigned long long old = cas_ar(&seg_of(h, cx)->link, link, pack(hi32(cur), x));
-        if (old == link) {
-          nxt = x;
-          cas_ar(&q->back.v, cur, pack(hi32(cur) + 1, x));
-          __threadfence();
-          vl_advance(h, c);
-        } else {
-          spare_push(h, c, x);
-          if (hi32(old) != hi32(cur)) { restart = true; break; }
-          nxt = lo32(old);
-        }
-      }
-      cur = pack(hi32(cur) + 1, nxt);
-    }
-    if (restart) continue;
-    st_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)], cur);
-    return seg_cells(h, lo32(cur)) + off;
+    cur = pack(hi32(cur) + 1, nxt);
   }
   set_error(h, OURO_ERR_TIMEOUT);
   return nullptr;

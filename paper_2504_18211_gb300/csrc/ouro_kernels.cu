@@ -124,12 +124,13 @@ __device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint
       uint32_t pv = __shfl_sync(0xffffffffu, incl, j + step - 1);
       if (u < total && pv <= u) j += step;
     }
-    const uint32_t before = j ? __shfl_sync(0xffffffffu, incl, (j - 1) & 31) : 0;
+    const uint32_t prev = __shfl_sync(0xffffffffu, incl, (j + 31) & 31);   /* every lane shuffles */
+    const uint32_t before = j ? prev : 0;
     unsigned long long bp = __shfl_sync(0xffffffffu, (unsigned long long)p, j & 31);
     uint32_t bsize = __shfl_sync(0xffffffffu, size, j & 31);
     uint32_t bkey = __shfl_sync(0xffffffffu, key, j & 31);
     if (u >= total) continue;
-    const uint32_t k = u - (j ? before : 0);    /* unit inside block j */
+    const uint32_t k = u - before;             /* unit inside block j */
     unsigned char *base = reinterpret_cast<unsigned char *>(bp) + 16ull * k;
     const uint32_t w0 = 4 * k, nw = bsize >> 2, tail = bsize & 3;
     if (w0 + 4 <= nw) {
