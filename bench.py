@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 device-side allocator on the size-sweep workload.
+
+Workload (one step): 2^20 requests on an 8 GiB heap cut into 8 KiB chunks;
+request i asks for 2^k bytes, k uniform in [4, 13] (seeded); every request
+allocates, writes its pattern, reads it back, checks it and frees -- one
+driver round of the paper's method (arXiv 2504.18211, Sec. 3) in one fused
+kernel.  value = malloc+free operations per second over the timed steps
+(2 x 2^20 ops per step), whole round included.
+
+Printed on one JSON line, besides the contract keys: the per-launch form
+(malloc / write / check / free kernels, whose malloc+free share is the
+paper's own timing), the virtualized-list variant, the malloc latency
+histogram (p50/p99), the measured L2 atomic rates and the allocator's
+fraction of them, the end-to-end figure with host buffers, and the CPU
+oracle on a bounded sample.
+
+--impl reference times the sequential CPU oracle (the stand-in for the
+paper's comparison system, which cannot run here) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "malloc+free Mops/s at 2^20 threads vs L2-atomic roofline; p99 alloc latency"
+UNIT = "Mops/s"
+HEAP_BYTES = 8 << 30
+CHUNK = 8192
+THREADS = 1 << 20
+SEED = 0x5EED
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--variant", default="page_array")
+    ap.add_argument("--threads", type=int, default=THREADS)
+    ap.add_argument("--heap-gib", type=int, default=HEAP_BYTES >> 30,
+                    help="heap size (smaller only for profiler captures)")
+    ap.add_argument("--no-extras", action="store_true", help="headline only (used under a profiler)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(threads, variant, form="fused", heap_bytes=HEAP_BYTES):
+    return {"workload": f"size sweep: {threads} requests of 2^k B (k uniform in [4,13], seeded), "
+                        f"allocate / write pattern / read back + check / free, one round per step",
+            "heap_bytes": heap_bytes, "chunk_bytes": CHUNK, "threads": threads, "variant": variant,
+            "form": form, "l2": "inputs larger than L2: ~1.7 GB of payload per round (L2 129 MB)"}
+
+
+# ----------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def classes_per_warp(sizes, chunk):
+    import numpy as np
+    s = sizes.astype(np.int64)
+    c = np.where(s <= 16, 0, np.ceil(np.log2(s)).astype(np.int64) - 4)
+    n = (c.size // 32) * 32
+    w = c[:n].reshape(-1, 32)
+    return float(np.mean([len(set(r)) for r in w[: min(len(w), 4096)]])), c
+
+
+# ---------------------------------------------------------------- CPU arm
+def cpu_oracle_sample(seconds: float, seed: int = SEED):
+    """The sequential oracle on a bounded sample of the same workload:
+    2^16 requests of the same size distribution on a 1 GiB heap (payload
+    written to host memory), rounds repeated for about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_2504_18211_gb300 import workloads as W
+    n = 1 << 16
+    sizes = W.sweep_sizes(n)
+    h = oracle.OracleHeap(1 << 30, CHUNK, "page_array")
+    mem = np.zeros(1 << 30, np.uint8)
+    lib, r = h.lib, oracle.RoundResult()
+    import ctypes as C
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    lib.orc_round(h.h, ptr(sizes), n, seed, 1, ptr(mem), None, C.byref(r))     # warm
+    rounds, t0 = 0, time.perf_counter()
+    while True:
+        lib.orc_round(h.h, ptr(sizes), n, seed, 1, ptr(mem), None, C.byref(r))
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    assert r.mismatches == 0 and r.nulls == 0
+    return {"value": round(rounds * 2 * n / el / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rounds} rounds of 2^16 requests (same size distribution, 1 GiB heap, payload in "
+                      f"host memory), one thread, {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import ctypes as C
+
+    import numpy as np
+
+    import oracle
+    from paper_2504_18211_gb300 import workloads as W
+    n = 1 << 16
+    sizes = W.sweep_sizes(n)
+    h = oracle.OracleHeap(1 << 30, CHUNK, args.variant)
+    mem = np.zeros(1 << 30, np.uint8)
+    r = oracle.RoundResult()
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    for _ in range(args.warmup):
+        h.lib.orc_round(h.h, ptr(sizes), n, SEED, 1, ptr(mem), None, C.byref(r))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h.lib.orc_round(h.h, ptr(sizes), n, SEED, 1, ptr(mem), None, C.byref(r))
+    el = time.perf_counter() - t0
+    value = args.steps * 2 * n / el / 1e6
+    sample = (f"each step: one round of 2^16 requests of the same size distribution (1 GiB heap, "
+              f"payload in host memory), sequential oracle, one thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(args.threads, args.variant),
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_2504_18211_gb300 as P
+    from paper_2504_18211_gb300 import build as B
+    from paper_2504_18211_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    P.load()
+
+    n = args.threads
+    sizes_np = W.sweep_sizes(n, seed=W.SEED_BASE + 1 + rank)      # each replica its own batch
+    sizes = torch.from_numpy(sizes_np.view(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+    ops_per_step = 2 * n
+
+    heap_bytes = args.heap_gib << 30
+    heap = P.Heap(heap_bytes, CHUNK, args.variant)
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        heap.round_fused(sizes, SEED, 1, out=out)
+    torch.cuda.synchronize()
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local).start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = P.ouro_kernel_launches()
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[2 * k].record(stream)
+        heap.round_fused(sizes, SEED, 1, out=out)
+        ev[2 * k + 1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = P.ouro_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps * ops_per_step / (total_ms / 1e3) / 1e6
+    chk = P.check_to_dict(out)
+    st = heap.stats()
+
+    import oracle
+    want = oracle.expected_checksums(sizes_np, SEED, 1)
+    verified = chk == dict(want, nulls=0, mismatches=0) and st["error_bits"] == 0
+
+    if rank != 0:
+        heap.close()
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    payload = int(sizes_np.astype(np.int64).sum())
+    meta_per_req = 37            # sizes 4 + malloc slot read/write 16 + chunk table 1 + free slot CAS 16
+    alg_bytes = 2 * payload + meta_per_req * n
+    mean_kernel_ms = statistics.mean(step_ms)
+    achieved = alg_bytes / (mean_kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
+                "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs", FALLBACK_HBM_GBS), 4),
+                "traffic": None, "kernel": "k_round_fused<page queues>",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)"}
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": workload_config(n, args.variant, "fused", heap_bytes), "verified": verified,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roofline}
+
+    if not args.no_extras:
+        line.update(extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk))
+        line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
+    heap.close()
+    print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def timed(torch, stream, fn, reps=1):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
+    stream = torch.cuda.current_stream()
+    ex = {}
+
+    # ---- end to end through the C ABI with host buffers
+    h_sizes = torch.from_numpy(sizes_np.view(np.int32)).pin_memory()
+    h_out = torch.zeros(5, dtype=torch.int64).pin_memory()
+    d_sizes = torch.empty_like(sizes)
+    out = torch.zeros(5, dtype=torch.int64, device="cuda")
+
+    def e2e_step():
+        d_sizes.copy_(h_sizes, non_blocking=True)
+        heap.round_fused(d_sizes, SEED, 1, out=out)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    ms = timed(torch, stream, e2e_step, args.steps)
+    ex["e2e"] = {"value": round(2 * n / (ms / 1e3) / 1e6, 3), "unit": UNIT,
+                 "h2d_bytes_per_step": int(h_sizes.numel() * 4), "d2h_bytes_per_step": 40}
+
+    # ---- per-launch form (the paper's protocol: time allocations and frees)
+    ptrs = torch.empty(n, dtype=torch.int64, device="cuda")
+    chk = torch.zeros(5, dtype=torch.int64, device="cuda")
+
+    def per_launch(variant_heap, reps):
+        tm = {"malloc": [], "write": [], "check": [], "free": []}
+        for _ in range(reps):
+            tm["malloc"].append(timed(torch, stream, lambda: variant_heap.malloc(sizes, ptrs)))
+            tm["write"].append(timed(torch, stream, lambda: P.pattern_write(ptrs, sizes, SEED, 1)))
+            tm["check"].append(timed(torch, stream, lambda: P.pattern_check(ptrs, sizes, SEED, 1, chk)))
+            tm["free"].append(timed(torch, stream, lambda: variant_heap.free(ptrs)))
+        return {k: statistics.mean(v[1:]) for k, v in tm.items()}
+
+    pl = per_launch(heap, 6)
+    af = pl["malloc"] + pl["free"]
+    round_ms = sum(pl.values())
+    ex["per_launch"] = {"ms": {k: round(v, 4) for k, v in pl.items()},
+                        "alloc_free_mops": round(2 * n / (af / 1e3) / 1e6, 1),
+                        "round_mops": round(2 * n / (round_ms / 1e3) / 1e6, 1)}
+
+    # ---- the other page-queue variant
+    others = {}
+    for v in ("page_array", "page_vlist"):
+        if v == args.variant:
+            continue
+        with P.Heap(HEAP_BYTES, CHUNK, v) as h2:
+            o2 = torch.zeros(5, dtype=torch.int64, device="cuda")
+            for _ in range(3):
+                h2.round_fused(sizes, SEED, 1, out=o2)
+            fms = timed(torch, stream, lambda: h2.round_fused(sizes, SEED, 1, out=o2), 5)
+            pl2 = per_launch(h2, 4)
+            ok = P.check_to_dict(o2)["mismatches"] == 0 and h2.stats()["error_bits"] == 0
+            others[v] = {"fused_mops": round(2 * n / (fms / 1e3) / 1e6, 1),
+                         "alloc_free_mops": round(2 * n / ((pl2["malloc"] + pl2["free"]) / 1e3) / 1e6, 1),
+                         "per_launch_ms": {k: round(x, 4) for k, x in pl2.items()}, "verified": ok}
+    ex["variants"] = others
+
+    # ---- malloc latency histogram (warm heap, malloc-only batch)
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    P.ouro_malloc_latency(heap.h, sizes, ptrs, hist)
+    heap.free(ptrs)
+    torch.cuda.synchronize()
+    hc = hist.cpu().numpy()
+    cum = np.cumsum(hc) / max(hc.sum(), 1)
+
+    def q(p):
+        b = int(np.searchsorted(cum, p))
+        lo, hi = P.B.latency_bin_bounds(b)
+        return (lo + hi) / 2
+
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    ex["alloc_latency"] = {"p50_cycles": q(0.50), "p99_cycles": q(0.99),
+                           "p50_ns": round(q(0.50) / mhz * 1e3, 1), "p99_ns": round(q(0.99) / mhz * 1e3, 1),
+                           "clock_mhz_for_ns": mhz, "clock_source": "median SM clock sampled in the timed region",
+                           "resolution": "log2 bins, 4 per octave (bin width 25% of its lower edge)",
+                           "load": f"{n} concurrent mallocs on a warm heap"}
+
+    # ---- L2 atomic rates and the allocator's share of them
+    words = 1 << 24
+    buf = torch.zeros(words, dtype=torch.int64, device="cuda")
+    blocks = 8 * torch.cuda.get_device_properties(0).multi_processor_count
+    rates = {}
+    for pat, iters in ((0, 32), (1, 64), (2, 64)):
+        P.ouro_probe_atomics(buf, pat, iters, blocks)
+        ms = timed(torch, stream, lambda: P.ouro_probe_atomics(buf, pat, iters, blocks), 3)
+        rates[pat] = blocks * 256 * iters / (ms / 1e3)
+    g, cls = classes_per_warp(sizes_np, CHUNK)
+    groups = n / 32 * g
+    max_class_groups = groups * max(np.bincount(cls, minlength=10)) / n
+    t_same = 2 * max_class_groups / rates[0]           # head (malloc) + tail (free) of the busiest class
+    t_dist = n / rates[2]                               # one slot CAS per free
+    roof_pairs = n / (t_same + t_dist)
+    ach_pairs = n / (af / 1e3)
+    ex["atomic_roofline"] = {
+        "rates_gops": {"same_address": round(rates[0] / 1e9, 3), "32_addresses": round(rates[1] / 1e9, 3),
+                       "distinct_cas": round(rates[2] / 1e9, 3)},
+        "classes_per_warp": round(g, 2), "roofline_mops": round(2 * roof_pairs / 1e6, 1),
+        "achieved_mops": round(2 * ach_pairs / 1e6, 1), "frac": round(ach_pairs / roof_pairs, 4),
+        "model": "per malloc+free pair: one same-address atomic per warp class group on head and on tail "
+                 "(busiest class serialises), one distinct-address slot CAS per free; per-launch timings"}
+    return ex
+
+
+if __name__ == "__main__":
+    main()

@@ -201,6 +201,23 @@ ouro_status ouro_pattern_check(void *const *d_ptrs, const uint32_t *d_sizes, siz
 ouro_status ouro_round_fused(ouro_heap *h, const uint32_t *d_sizes, size_t n, uint32_t seed,
                              int mode, ouro_check *d_out, void **d_ptrs, void *stream);
 
+/* ---- measurement ------------------------------------------------------------ */
+
+/* L2 atomic throughput probe: `blocks` x 256 threads each do `iters` atomics on
+ * d_buf (device, `words` 64-bit words >= 512, contents overwritten).
+ * pattern 0: one shared counter; 1: 32 counters on separate 128-byte lines;
+ * 2: distinct words, consecutive lanes on consecutive words, 64-bit CAS.
+ * Time it with events on `stream`. */
+ouro_status ouro_probe_atomics(unsigned long long *d_buf, size_t words, int pattern, uint32_t iters,
+                               int blocks, void *stream);
+
+/* As ouro_batch_malloc, timing every request with clock64: d_hist (device,
+ * 256 words, overwritten) counts requests per latency bin; bin b < 4 holds
+ * b cycles, bin b >= 4 holds [2^l + q*2^(l-2), 2^l + (q+1)*2^(l-2)) cycles
+ * with l = b >> 2, q = b & 3. */
+ouro_status ouro_malloc_latency(ouro_heap *h, const uint32_t *d_sizes, void **d_ptrs, size_t n,
+                                unsigned long long *d_hist, void *stream);
+
 /* ---- misc ----------------------------------------------------------------- */
 const char *ouro_status_string(ouro_status s);
 int ouro_last_cuda_error(void);

@@ -12,8 +12,8 @@ from ._binding import (CHUNK_ARRAY, CHUNK_VLIST, PAGE_ARRAY, PAGE_VLIST, VARIANT
                        OuroError, check_to_dict, load, ouro_batch_free, ouro_batch_malloc,
                        ouro_debug_stall_producer, ouro_heap_create_ex, ouro_heap_destroy,
                        ouro_heap_device, ouro_heap_reset, ouro_heap_snapshot, ouro_heap_stats,
-                       ouro_heap_trim, ouro_kernel_launches, ouro_pattern_check, ouro_pattern_write,
-                       ouro_round_fused, ouro_status_string)
+                       ouro_heap_trim, ouro_kernel_launches, ouro_malloc_latency, ouro_pattern_check,
+                       ouro_pattern_write, ouro_probe_atomics, ouro_round_fused, ouro_status_string)
 
 
 class Heap:

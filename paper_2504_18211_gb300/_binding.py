@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
         "ouro_last_cuda_error": (i32, []),
         "ouro_kernel_launches": (u64, []),
         "ouro_debug_stall_producer": (st, [vp, i32, u32, vp]),
+        "ouro_probe_atomics": (st, [vp, sz, i32, u32, i32, vp]),
+        "ouro_malloc_latency": (st, [vp, vp, vp, sz, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -227,3 +229,21 @@ def check_to_dict(t) -> dict:
     m = (1 << 64) - 1
     return {"nulls": v[0] & m, "mismatches": v[1] & m, "xor64": v[2] & m, "sum64": v[3] & m,
             "words": v[4] & m}
+
+
+def ouro_probe_atomics(buf, pattern: int, iters: int, blocks: int, stream=None) -> None:
+    _check("ouro_probe_atomics", load().ouro_probe_atomics(_ptr(buf), buf.numel(), pattern, iters, blocks,
+                                                            _stream(stream)))
+
+
+def ouro_malloc_latency(h: int, sizes, ptrs, hist, stream=None) -> None:
+    _check("ouro_malloc_latency", load().ouro_malloc_latency(C.c_void_p(h), _ptr(sizes), _ptr(ptrs),
+                                                              sizes.numel(), _ptr(hist), _stream(stream)))
+
+
+def latency_bin_bounds(b: int):
+    """[lo, hi) cycles of histogram bin b of ouro_malloc_latency."""
+    if b < 4:
+        return b, b + 1
+    l, q = b >> 2, b & 3
+    return (1 << l) + q * (1 << (l - 2)), (1 << l) + (q + 1) * (1 << (l - 2))

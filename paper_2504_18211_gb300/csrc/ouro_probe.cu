@@ -1,0 +1,99 @@
+/*
+ * Measurement kernels: the L2 atomic rates that bound the allocator, and a
+ * per-request malloc latency histogram.
+ *
+ * The allocator's queue traffic is atomics: one same-address atomic per
+ * warp group on a class head or tail counter, one distinct-address
+ * compare-and-swap per lane on a queue slot.  ouro_probe_atomics measures
+ * those two rates on the running GPU so the bench can state achieved
+ * allocator throughput as a fraction of them.
+ */
+#include "ouro_internal.cuh"
+
+using namespace ouro::detail;
+
+namespace {
+
+/* pattern 0: every thread, one 64-bit counter (returning atomicAdd)
+ * pattern 1: every thread, one of 32 counters on separate lines
+ * pattern 2: distinct addresses, consecutive lanes on consecutive words
+ *            (like queue slots), 64-bit CAS that always succeeds */
+__global__ void k_probe(unsigned long long *buf, unsigned long long words, int pattern, unsigned iters,
+                        unsigned long long *sink) {
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long acc = 0;
+  if (pattern == 0) {
+    for (unsigned i = 0; i < iters; ++i) acc += atomicAdd(&buf[0], 1ull);
+  } else if (pattern == 1) {
+    unsigned long long *p = &buf[(tid & 31) * 16];
+    for (unsigned i = 0; i < iters; ++i) acc += atomicAdd(p, 1ull);
+  } else {
+    for (unsigned i = 0; i < iters; ++i) {
+      unsigned long long w = (tid + (unsigned long long)i * nthreads) % words;
+      unsigned long long v = buf[w];
+      acc += atomicCAS(&buf[w], v, v + 1);
+    }
+  }
+  if (acc == 0x5A5A5A5A5A5A5A5Aull) *sink = acc;   /* keeps the loop alive */
+}
+
+/* clock64 around every malloc: 4 sub-buckets per octave of cycles */
+__device__ __forceinline__ unsigned lat_bin(unsigned long long d) {
+  if (d < 4) return (unsigned)d;
+  const unsigned l = 63 - __clzll(d);
+  return (l << 2) | (unsigned)((d >> (l - 2)) & 3);
+}
+
+template <int V>
+__global__ void k_malloc_timed(ouro_heap_dev h, const uint32_t *sizes, void **ptrs, size_t n,
+                               unsigned long long *hist) {
+  __shared__ unsigned long long sh[256];
+  for (unsigned i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long t0 = clock64();
+    void *p;
+    {
+      const unsigned mask = __activemask();
+      const int cls = size_class(h, sizes[i]);
+      const unsigned vmask = __ballot_sync(mask, cls >= 0);
+      p = cls >= 0 ? page_malloc<V>(h, cls, vmask) : nullptr;
+    }
+    const unsigned long long t1 = clock64();
+    ptrs[i] = p;
+    atomicAdd(&sh[min(lat_bin(t1 - t0), 255u)], 1ull);
+  }
+  __syncthreads();
+  for (unsigned i = threadIdx.x; i < 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" ouro_status ouro_probe_atomics(unsigned long long *d_buf, size_t words, int pattern, uint32_t iters,
+                                          int blocks, void *stream) {
+  if (!d_buf || words < 32 * 16 || pattern < 0 || pattern > 2 || blocks <= 0) return OURO_EINVAL;
+  k_probe<<<blocks, 256, 0, S(stream)>>>(d_buf, words, pattern, iters, d_buf + words - 1);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_malloc_latency(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n,
+                                           unsigned long long *d_hist, void *stream) {
+  if (!H || !d_hist || (n && (!d_sizes || !d_ptrs))) return OURO_EINVAL;
+  OURO_CUDA(cudaMemsetAsync(d_hist, 0, 256 * 8, S(stream)));
+  if (!n) return OURO_OK;
+  const int block = 256;
+  size_t g = (n + block - 1) / block;
+  if (g > (1u << 20)) g = 1u << 20;
+  switch (H->d.variant) {
+    case OURO_PAGE_ARRAY: k_malloc_timed<OURO_PAGE_ARRAY><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
+    case OURO_PAGE_VLIST: k_malloc_timed<OURO_PAGE_VLIST><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
+    default: return OURO_ENOTSUP;
+  }
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
