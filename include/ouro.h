@@ -201,6 +201,26 @@ ouro_status ouro_pattern_check(void *const *d_ptrs, const uint32_t *d_sizes, siz
 ouro_status ouro_round_fused(ouro_heap *h, const uint32_t *d_sizes, size_t n, uint32_t seed,
                              int mode, ouro_check *d_out, void **d_ptrs, void *stream);
 
+/* Same result as ouro_heap_stats, for callers that cannot allocate device
+ * memory when they ask: code running while a CUDA stream capture is open
+ * (cudaMalloc is not allowed there) or applications whose device memory is
+ * all handed out up front by their own pool.  The paper has no counterpart;
+ * this is a service of this library.
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *     call.  Its scratch (1584 bytes) is a file-scope __device__ array that
+ *     every GPU loading the library keeps until the process exits.
+ *   - Limit: heaps of at most OURO_MAX_CLASSES size classes (chunks up to
+ *     1 MiB); a larger heap is rejected with OURO_EINVAL.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (it is cleared at the start of every call): calls that overlap on the
+ *     GPU (other streams, other threads) race and may return mixed counts.
+ *   - Syncs `stream`; returns OURO_EDEVICE (after filling *out) when the
+ *     device error word is non-zero. */
+ouro_status ouro_heap_stats_static(ouro_heap *h, ouro_stats *out, void *stream);
+
 /* ---- measurement ------------------------------------------------------------ */
 
 /* L2 atomic throughput probe: `blocks` x 256 threads each do `iters` atomics on

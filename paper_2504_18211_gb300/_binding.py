@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "ouro_debug_stall_producer": (st, [vp, i32, u32, vp]),
         "ouro_probe_atomics": (st, [vp, sz, i32, u32, i32, vp]),
         "ouro_malloc_latency": (st, [vp, vp, vp, sz, vp, vp]),
+        "ouro_heap_stats_static": (st, [vp, C.POINTER(Stats), vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -150,6 +151,24 @@ def ouro_heap_device(h: int) -> HeapDev:
     d = HeapDev()
     _check("ouro_heap_device", load().ouro_heap_device(C.c_void_p(h), C.byref(d)))
     return d
+
+
+def _stats_dict(s: Stats) -> dict:
+    nc = s.n_classes
+    out = {k: [int(x) for x in getattr(s, k)[:nc]] for k in
+           ("mallocs", "frees", "failed", "carves", "carved_now", "queued", "live", "repushes", "dead")}
+    for k in ("zero_reqs", "too_large", "bump", "pool_size", "seg_chunks", "spare_chunks",
+              "error_bits", "n_classes"):
+        out[k] = int(getattr(s, k))
+    return out
+
+
+def ouro_heap_stats_static(h: int, stream=None) -> dict:
+    """ouro_heap_stats without any device allocation (scratch in a static device array)."""
+    s = Stats()
+    _check("ouro_heap_stats_static", load().ouro_heap_stats_static(C.c_void_p(h), C.byref(s), _stream(stream)),
+           ok=(0, 4))
+    return _stats_dict(s)
 
 
 def ouro_heap_stats(h: int, stream=None) -> dict:

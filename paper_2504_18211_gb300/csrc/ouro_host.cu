@@ -9,6 +9,7 @@
  */
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ouro_internal.cuh"
@@ -718,4 +719,90 @@ extern "C" ouro_status ouro_debug_stall_producer(ouro_heap *H, int cls, uint32_t
   k_stall_producer<<<1, 1, 0, S(stream)>>>(H->d, cls, n);
   OURO_LAUNCHED();
   return OURO_OK;
+}
+
+/* ------------------------------------------- statistics without allocation */
+/* For callers that must not allocate device memory at the time they ask for
+ * statistics, e.g. code running while a CUDA stream capture is open (where
+ * cudaMalloc is not permitted) or applications whose device memory is all
+ * handed out up front by their own pool.  The scratch lives in this file-scope
+ * device array instead of a cudaMalloc'ed buffer; every device that loads the
+ * library holds it (1.5 KiB) until the process exits. */
+#define OURO_STATIC_SCRATCH_ROWS (OURO_MAX_CLASSES + 1)
+#define OURO_STATIC_SCRATCH_WORDS (OURO_STATIC_SCRATCH_ROWS * (OURO_NSTAT + 3))
+static __device__ __align__(256) unsigned long long g_stats_scratch[OURO_STATIC_SCRATCH_WORDS];
+
+/* sum the per-SM shards of every counter row into out[row * OURO_NSTAT + kind] */
+__global__ void k_sum_shards(ouro_heap_dev h, unsigned long long *out) {
+  const unsigned rows = (h.n_classes + 1) * OURO_NSTAT;
+  for (unsigned i = threadIdx.x; i < rows; i += blockDim.x) {
+    unsigned long long a = 0;
+    for (unsigned s = 0; s < OURO_SHARDS; ++s) a += h.stats[(size_t)i * OURO_SHARDS + s];
+    out[i] = a;
+  }
+}
+
+static std::mutex g_scratch_mu;
+static unsigned long long *g_scratch_dev[64];   /* device address of the array, per device ordinal */
+
+extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, void *stream) {
+  if (!H || !out) return OURO_EINVAL;
+  const ouro_heap_dev &d = H->d;
+  if (d.n_classes + 1 > OURO_STATIC_SCRATCH_ROWS) return OURO_EINVAL;   /* larger than the scratch array */
+  int dev = 0;
+  OURO_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return OURO_EINVAL;
+  unsigned long long *scratch;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+      void *p = nullptr;
+      OURO_CUDA(cudaGetSymbolAddress(&p, g_stats_scratch));
+      g_scratch_dev[dev] = (unsigned long long *)p;
+    }
+    scratch = g_scratch_dev[dev];
+  }
+  cudaStream_t s = S(stream);
+  const unsigned R = OURO_STATIC_SCRATCH_ROWS;
+  unsigned long long *dsum = scratch, *dq = scratch + R * OURO_NSTAT, *dh = dq + R, *ds = dh + R;
+  OURO_CUDA(cudaMemsetAsync(scratch, 0, OURO_STATIC_SCRATCH_WORDS * 8, s));
+  k_sum_shards<<<1, 256, 0, s>>>(d, dsum);
+  OURO_LAUNCHED();
+  k_count_queued<<<d.n_classes, 256, 0, s>>>(d, dq);
+  OURO_LAUNCHED();
+  k_chunk_hist<<<2 * sm_count(), 256, 0, s>>>(d, dh);
+  OURO_LAUNCHED();
+  if (is_vlist(d.variant)) {
+    k_count_spares<<<1, 32, 0, s>>>(d, ds);
+    OURO_LAUNCHED();
+  }
+  unsigned long long hv[OURO_STATIC_SCRATCH_WORDS];
+  ouro_glob g;
+  OURO_CUDA(cudaMemcpyAsync(hv, scratch, sizeof(hv), cudaMemcpyDeviceToHost, s));
+  OURO_CUDA(cudaMemcpyAsync(&g, d.glob, sizeof(g), cudaMemcpyDeviceToHost, s));
+  OURO_CUDA(cudaStreamSynchronize(s));
+  const unsigned long long *hs = hv, *hq = hv + R * OURO_NSTAT, *hh = hq + R, *hsp = hh + R;
+  memset(out, 0, sizeof(*out));
+  out->n_classes = d.n_classes;
+  for (unsigned c = 0; c < d.n_classes; ++c) {
+    const unsigned long long *row = hs + (size_t)c * OURO_NSTAT;
+    out->mallocs[c] = row[OURO_ST_MALLOC];
+    out->frees[c] = row[OURO_ST_FREE];
+    out->failed[c] = row[OURO_ST_FAILED];
+    out->carves[c] = row[OURO_ST_CARVE];
+    out->repushes[c] = row[OURO_ST_REPUSH];
+    out->dead[c] = row[OURO_ST_DEAD];
+    out->live[c] = out->mallocs[c] - out->frees[c];
+    out->queued[c] = hq[c];
+    out->carved_now[c] = hh[c];
+    out->spare_chunks += hsp[c];
+  }
+  out->seg_chunks = hh[OURO_MAX_CLASSES];
+  if (out->seg_chunks >= out->spare_chunks) out->seg_chunks -= out->spare_chunks;
+  out->zero_reqs = hs[(size_t)d.n_classes * OURO_NSTAT + OURO_ST_ZERO];
+  out->too_large = hs[(size_t)d.n_classes * OURO_NSTAT + OURO_ST_TOO_LARGE];
+  out->bump = g.bump.v < d.n_chunks ? g.bump.v : d.n_chunks;
+  out->pool_size = g.pool_taken.v < g.pool_size ? g.pool_size - g.pool_taken.v : 0;
+  out->error_bits = g.error_bits;
+  return g.error_bits ? OURO_EDEVICE : OURO_OK;
 }
