@@ -225,8 +225,10 @@ ouro_status ouro_heap_stats_static(ouro_heap *h, ouro_stats *out, void *stream);
 
 /* L2 atomic throughput probe: `blocks` x 256 threads each do `iters` atomics on
  * d_buf (device, `words` 64-bit words >= 512, contents overwritten).
- * pattern 0: one shared counter; 1: 32 counters on separate 128-byte lines;
- * 2: distinct words, consecutive lanes on consecutive words, 64-bit CAS.
+ * pattern 0: lane 0 of every warp on one shared counter; 1: lane 0 of every
+ * warp on one of 32 counters on separate 128-byte lines (one atomic per warp,
+ * as a warp group leader issues); 2: every lane, distinct words, consecutive
+ * lanes on consecutive words, 64-bit CAS.
  * Time it with events on `stream`. */
 ouro_status ouro_probe_atomics(unsigned long long *d_buf, size_t words, int pattern, uint32_t iters,
                                int blocks, void *stream);

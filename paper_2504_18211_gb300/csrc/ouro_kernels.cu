@@ -87,20 +87,69 @@ struct acc {
   }
 };
 
-/* Warp-cooperative payload over the 32 blocks of a warp.  Every lane of the
- * warp must call (a lane without a block passes p = null).  write: store
- * the pattern; check: read back, compare, fold checksums into a.
+/* Warp-cooperative payload over the 32 blocks of a warp, one block at a
+ * time: all 32 lanes stride over the block's 16-byte units, several units in
+ * flight per lane.  Every lane of the warp must call (a lane without a block
+ * passes p = null).
+ *   WRITE:  store the pattern.
+ *   CHECK:  read back, compare, fold the checksums into a.
+ *   FUSED:  write the block, then (after __syncwarp) read it back through L2
+ *           with every lane checking the units its neighbour wrote.
  * mode 0: word 0 = tid.  mode 1: floor(size/4) words key + w*GOLD, then the
  * low size%4 bytes of word floor(size/4). */
+enum { PAY_WRITE = 1, PAY_CHECK = 2, PAY_FUSED = 3 };
+
+__device__ __forceinline__ uint4 pat4(uint32_t key, uint32_t w0) {
+  return make_uint4(key + w0 * OURO_GOLD, key + (w0 + 1) * OURO_GOLD, key + (w0 + 2) * OURO_GOLD,
+                    key + (w0 + 3) * OURO_GOLD);
+}
+
+__device__ __forceinline__ void check4(const uint4 &got, const uint4 &want, acc &a) {
+  a.mism += (got.x != want.x) + (got.y != want.y) + (got.z != want.z) + (got.w != want.w);
+  a.x ^= (unsigned long long)(got.x ^ got.y ^ got.z ^ got.w);
+  a.s += (unsigned long long)got.x + got.y + got.z + got.w;
+  a.words += 4;
+}
+
+/* words [4*units, nw) and the tail bytes of one block: one lane */
 template <bool WRITE>
-__device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint32_t seed, int mode,
-                             acc &a) {
+__device__ void block_rest(unsigned char *bp, uint32_t key, uint32_t nw, uint32_t tail, acc &a) {
+  uint32_t *wp = reinterpret_cast<uint32_t *>(bp);
+  for (uint32_t w = nw & ~3u; w < nw; ++w) {
+    const uint32_t want = key + w * OURO_GOLD;
+    if (WRITE) wp[w] = want;
+    else {
+      uint32_t got = __ldcg(wp + w);
+      a.mism += got != want;
+      a.fold(got);
+    }
+  }
+  if (tail) {
+    const uint32_t v = key + nw * OURO_GOLD;
+    unsigned char *tb = bp + 4ull * nw;
+    if (WRITE) {
+      for (uint32_t b = 0; b < tail; ++b) tb[b] = (unsigned char)(v >> (8 * b));
+    } else {
+      uint32_t got = 0;
+      for (uint32_t b = 0; b < tail; ++b) {
+        unsigned char gb = __ldcg(tb + b);
+        a.mism += gb != (unsigned char)(v >> (8 * b));
+        got |= (uint32_t)gb << (8 * b);
+      }
+      a.fold(got);
+    }
+  }
+}
+
+template <int OP>
+__device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint32_t seed, int mode, acc &a) {
   const unsigned lane = laneid();
   if (mode == 0) {
     if (p) {
-      if (WRITE) *reinterpret_cast<uint32_t *>(p) = tid;
-      else {
-        uint32_t v = *reinterpret_cast<const uint32_t *>(p);
+      if (OP & PAY_WRITE) *reinterpret_cast<uint32_t *>(p) = tid;
+      if (OP == PAY_FUSED) __syncwarp(__activemask());
+      if (OP & PAY_CHECK) {
+        uint32_t v = __ldcg(reinterpret_cast<const uint32_t *>(p));
         a.mism += v != tid;
         a.fold(v);
       }
@@ -108,70 +157,34 @@ __device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint
     return;
   }
   const uint32_t key = fmix32(seed ^ (tid * OURO_GOLD));
-  const uint32_t units = p ? (size + 15) >> 4 : 0;
-  /* inclusive prefix of units over the warp */
-  uint32_t incl = units;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((int)lane >= o) incl += v;
-  }
-  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  for (uint32_t u0 = 0; u0 < total; u0 += 32) {
-    const uint32_t u = u0 + lane;
-    /* block j = number of lanes whose inclusive prefix is <= u */
-    int j = 0;
-    for (int step = 16; step; step >>= 1) {
-      uint32_t pv = __shfl_sync(0xffffffffu, incl, j + step - 1);
-      if (u < total && pv <= u) j += step;
+  const unsigned rd = OP == PAY_FUSED ? (lane + 1) & 31 : lane;   /* unit lane that this lane checks */
+  for (int j = 0; j < 32; ++j) {
+    const unsigned long long bpi = __shfl_sync(0xffffffffu, (unsigned long long)p, j);
+    const uint32_t bsize = __shfl_sync(0xffffffffu, size, j);
+    const uint32_t bkey = __shfl_sync(0xffffffffu, key, j);
+    if (!bpi) continue;
+    unsigned char *bp = reinterpret_cast<unsigned char *>(bpi);
+    uint4 *u4 = reinterpret_cast<uint4 *>(bp);
+    const uint32_t nw = bsize >> 2, tail = bsize & 3, units = nw >> 2;
+    const unsigned rest_lane = units & 31;
+    if (OP & PAY_WRITE) {
+#pragma unroll 4
+      for (uint32_t u = lane; u < units; u += 32) u4[u] = pat4(bkey, 4 * u);
+      if (lane == rest_lane) block_rest<true>(bp, bkey, nw, tail, a);
     }
-    const uint32_t prev = __shfl_sync(0xffffffffu, incl, (j + 31) & 31);   /* every lane shuffles */
-    const uint32_t before = j ? prev : 0;
-    unsigned long long bp = __shfl_sync(0xffffffffu, (unsigned long long)p, j & 31);
-    uint32_t bsize = __shfl_sync(0xffffffffu, size, j & 31);
-    uint32_t bkey = __shfl_sync(0xffffffffu, key, j & 31);
-    if (u >= total) continue;
-    const uint32_t k = u - before;             /* unit inside block j */
-    unsigned char *base = reinterpret_cast<unsigned char *>(bp) + 16ull * k;
-    const uint32_t w0 = 4 * k, nw = bsize >> 2, tail = bsize & 3;
-    if (w0 + 4 <= nw) {
-      uint4 want = make_uint4(bkey + w0 * OURO_GOLD, bkey + (w0 + 1) * OURO_GOLD,
-                              bkey + (w0 + 2) * OURO_GOLD, bkey + (w0 + 3) * OURO_GOLD);
-      if (WRITE) {
-        *reinterpret_cast<uint4 *>(base) = want;
-      } else {
-        uint4 got = *reinterpret_cast<const uint4 *>(base);
-        a.mism += (got.x != want.x) + (got.y != want.y) + (got.z != want.z) + (got.w != want.w);
-        a.fold(got.x);
-        a.fold(got.y);
-        a.fold(got.z);
-        a.fold(got.w);
+    if (OP == PAY_FUSED) __syncwarp();
+    if (OP & PAY_CHECK) {
+      uint32_t u = rd;
+      for (; u + 96 < units; u += 128) {          /* four independent 16-byte loads in flight */
+        const uint4 g0 = __ldcg(u4 + u), g1 = __ldcg(u4 + u + 32), g2 = __ldcg(u4 + u + 64),
+                    g3 = __ldcg(u4 + u + 96);
+        check4(g0, pat4(bkey, 4 * u), a);
+        check4(g1, pat4(bkey, 4 * (u + 32)), a);
+        check4(g2, pat4(bkey, 4 * (u + 64)), a);
+        check4(g3, pat4(bkey, 4 * (u + 96)), a);
       }
-    } else {
-      uint32_t *wp = reinterpret_cast<uint32_t *>(base);
-      for (uint32_t w = w0; w < nw && w < w0 + 4; ++w) {
-        const uint32_t want = bkey + w * OURO_GOLD;
-        if (WRITE) wp[w - w0] = want;
-        else {
-          uint32_t got = wp[w - w0];
-          a.mism += got != want;
-          a.fold(got);
-        }
-      }
-      if (tail && nw < w0 + 4) {
-        const uint32_t v = bkey + nw * OURO_GOLD;
-        unsigned char *tb = reinterpret_cast<unsigned char *>(bp) + 4ull * nw;
-        if (WRITE) {
-          for (uint32_t b = 0; b < tail; ++b) tb[b] = (unsigned char)(v >> (8 * b));
-        } else {
-          uint32_t got = 0;
-          for (uint32_t b = 0; b < tail; ++b) {
-            unsigned char gb = tb[b];
-            a.mism += gb != (unsigned char)(v >> (8 * b));
-            got |= (uint32_t)gb << (8 * b);
-          }
-          a.fold(got);
-        }
-      }
+      for (; u < units; u += 32) check4(__ldcg(u4 + u), pat4(bkey, 4 * u), a);
+      if (lane == (OP == PAY_FUSED ? (rest_lane + 31) & 31 : rest_lane)) block_rest<false>(bp, bkey, nw, tail, a);
     }
   }
 }
@@ -205,7 +218,7 @@ __device__ void flush_acc(acc &a, unsigned long long nulls, ouro_check *out) {
   }
 }
 
-template <bool WRITE>
+template <int OP>
 __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, uint32_t seed, int mode,
                           ouro_check *out) {
   acc a;
@@ -217,14 +230,14 @@ __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, ui
     unsigned char *p = i < n ? static_cast<unsigned char *>(ptrs[i]) : nullptr;
     const uint32_t sz = i < n ? sizes[i] : 0;
     if (i < n && !p) nulls++;
-    warp_payload<WRITE>(p, sz, (uint32_t)i, seed, mode, a);
+    warp_payload<OP>(p, sz, (uint32_t)i, seed, mode, a);
   }
-  if (!WRITE) flush_acc(a, nulls, out);
+  if (OP & PAY_CHECK) flush_acc(a, nulls, out);
 }
 
 /* one whole round per thread: malloc, write, read back, free */
 template <int V>
-__global__ void __launch_bounds__(256) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
+__global__ void __launch_bounds__(256, 4) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
                                                      uint32_t seed, int mode, ouro_check *out, void **ptrs) {
   acc a;
   unsigned long long nulls = 0;
@@ -240,9 +253,7 @@ __global__ void __launch_bounds__(256) k_round_fused(ouro_heap_dev h, const uint
       if (ptrs) ptrs[i] = p;
     }
     __syncwarp();
-    warp_payload<true>(p, sz, (uint32_t)i, seed, mode, a);
-    __syncwarp();
-    warp_payload<false>(p, sz, (uint32_t)i, seed, mode, a);
+    warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed, mode, a);
     __syncwarp();
     if (i < n) free_v<V>(h, p);
     __syncwarp();
@@ -311,8 +322,8 @@ extern "C" ouro_status ouro_pattern_write(void *const *d_ptrs, const uint32_t *d
   if (mode != 0 && mode != 1) return OURO_EINVAL;
   if (!n) return OURO_OK;
   const int block = 256;
-  const int g = grid_for((n + 31) / 32 * 32, block, occupancy_grid(k_pattern<true>, block));
-  k_pattern<true><<<g, block, 0, S(stream)>>>(d_ptrs, d_sizes, n, seed, mode, nullptr);
+  const int g = grid_for((n + 31) / 32 * 32, block, occupancy_grid(k_pattern<PAY_WRITE>, block));
+  k_pattern<PAY_WRITE><<<g, block, 0, S(stream)>>>(d_ptrs, d_sizes, n, seed, mode, nullptr);
   OURO_LAUNCHED();
   return OURO_OK;
 }
@@ -324,8 +335,8 @@ extern "C" ouro_status ouro_pattern_check(void *const *d_ptrs, const uint32_t *d
   OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
   if (!n) return OURO_OK;
   const int block = 256;
-  const int g = grid_for((n + 31) / 32 * 32, block, occupancy_grid(k_pattern<false>, block));
-  k_pattern<false><<<g, block, 0, S(stream)>>>(d_ptrs, d_sizes, n, seed, mode, d_out);
+  const int g = grid_for((n + 31) / 32 * 32, block, occupancy_grid(k_pattern<PAY_CHECK>, block));
+  k_pattern<PAY_CHECK><<<g, block, 0, S(stream)>>>(d_ptrs, d_sizes, n, seed, mode, d_out);
   OURO_LAUNCHED();
   return OURO_OK;
 }

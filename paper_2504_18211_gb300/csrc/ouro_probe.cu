@@ -14,20 +14,25 @@ using namespace ouro::detail;
 
 namespace {
 
-/* pattern 0: every thread, one 64-bit counter (returning atomicAdd)
- * pattern 1: every thread, one of 32 counters on separate lines
+/* pattern 0: lane 0 of every warp, one 64-bit counter (returning atomicAdd),
+ *            as a warp group leader on a class head or tail
+ * pattern 1: lane 0 of every warp, one of 32 counters on separate lines
  * pattern 2: distinct addresses, consecutive lanes on consecutive words
- *            (like queue slots), 64-bit CAS that always succeeds */
+ *            (like queue slots), 64-bit CAS that always succeeds
+ * (an atomic issued by all 32 lanes on one address is merged by the
+ * hardware, so patterns 0 and 1 issue one atomic per warp) */
 __global__ void k_probe(unsigned long long *buf, unsigned long long words, int pattern, unsigned iters,
                         unsigned long long *sink) {
   const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned long long nthreads = (unsigned long long)gridDim.x * blockDim.x;
   unsigned long long acc = 0;
   if (pattern == 0) {
-    for (unsigned i = 0; i < iters; ++i) acc += atomicAdd(&buf[0], 1ull);
+    if ((threadIdx.x & 31) == 0)
+      for (unsigned i = 0; i < iters; ++i) acc += atomicAdd(&buf[0], 1ull);
   } else if (pattern == 1) {
-    unsigned long long *p = &buf[(tid & 31) * 16];
-    for (unsigned i = 0; i < iters; ++i) acc += atomicAdd(p, 1ull);
+    unsigned long long *p = &buf[((tid >> 5) & 31) * 16];
+    if ((threadIdx.x & 31) == 0)
+      for (unsigned i = 0; i < iters; ++i) acc += atomicAdd(p, 1ull);
   } else {
     for (unsigned i = 0; i < iters; ++i) {
       unsigned long long w = (tid + (unsigned long long)i * nthreads) % words;
