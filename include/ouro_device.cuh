@@ -693,6 +693,398 @@ __device__ __forceinline__ int locate(const ouro_heap_dev &h, const void *p, uns
   return (int)c;
 }
 
+/* ------------------------------------------------------- chunk queues */
+/* Chunk queues (Sec. 4.2): a class queue holds ids of chunks that have free
+ * pages; a malloc obtains a chunk id, then claims free pages of that chunk
+ * from its bitmap.  GB300 form: a warp group POPS a chunk id (one position,
+ * like a page queue), reserves pages with one atomicSub on the chunk's free
+ * count, claims the bits, and pushes the chunk back while it still has free
+ * pages; a chunk is in its queue at most once.  A free sets the bit, adds to
+ * the count, and the increment that lifts the count from <= 0 to >= 1 queues
+ * the chunk again.  Carving packs the page needs that waiting groups posted
+ * in their empty slots into fresh chunks, with those pages reserved, so the
+ * number of chunks carved for a malloc-only burst follows the demand. */
+
+/* slot item of a chunk queue: chunk id, or a reserved fill
+ * (bit 31 | (reserved pages - 1) << 26 | chunk id) */
+#define OURO_CQ_RES 0x80000000u
+#define OURO_CQ_ID(it) ((it) & ((1u << 26) - 1))
+#define OURO_CQ_CNT(it) ((((it) >> 26) & 31u) + 1)
+
+template <bool VL>
+__device__ inline void chunk_push(const ouro_heap_dev &h, int c, unsigned x) {
+  push_one<VL>(h, c, x);
+}
+
+/* Called by every lane of vmask; lane `owner` holds the carve lock of class c. */
+template <int V>
+__device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
+  constexpr bool VL = (V == OURO_CHUNK_VLIST);
+  ouro_qhdr *q = qh(h, c);
+  const unsigned lane = laneid();
+  const unsigned ppc_log = h.log2_chunk - 4 - c;
+  const unsigned ppc = 1u << ppc_log;
+  const unsigned words_c = (ppc + 31) >> 5;
+  const unsigned nl = __popc(vmask), rk = __popc(vmask & lanemask_lt());
+  const bool full_warp = vmask == 0xffffffffu;
+  for (int batch = 0; batch < 64; ++batch) {
+    /* 1. the debt positions of this batch, claimed as producer */
+    unsigned long long t = 0, hd = 0;
+    unsigned D = 0;
+    if ((int)lane == owner) {
+      for (unsigned it = 0; it < 64; ++it) {
+        t = ld_acq(&q->tail.v);
+        hd = ld_acq(&q->head.v);
+        if (hd <= t) break;
+        unsigned d = (unsigned)min(hd - t, 8ull * nl);   /* each lane plans up to 8 positions */
+        if (VL) vl_slot(h, c, t + d - 1, true);           /* segments before chunks */
+        if (atomicCAS(&q->tail.v, t, t + d) == t) { D = d; break; }
+      }
+    }
+    D = __shfl_sync(vmask, D, owner);
+    if (!D) break;
+    t = __shfl_sync(vmask, t, owner);
+    /* 2. posted needs (an unposted slot counts as a full warp) and their prefix sum */
+    unsigned need[8];
+    unsigned long long *cell[8];
+    unsigned excl[8];
+    unsigned running = 0;
+    for (int r = 0; r < 8; ++r) {
+      const unsigned i = rk + (unsigned)r * nl;
+      need[r] = 0;
+      cell[r] = nullptr;
+      if (i < D) {
+        cell[r] = slot_at<VL>(h, c, t + i, true);
+        unsigned long long v = cell[r] ? ld_acq(cell[r]) : 0;
+        unsigned posted = (cell[r] && slot_d(v, t + i) == 0) ? lo32(v) : 0;
+        need[r] = posted ? min(posted, 32u) : 32u;
+      }
+      /* inclusive scan over the lanes of vmask (positions rk + r*nl are in lane order) */
+      unsigned x = need[r];
+      if (full_warp) {
+        for (int o = 1; o < 32; o <<= 1) {
+          unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+          if ((int)lane >= o) x += y;
+        }
+      } else {
+        /* sparse warp: gather through the lanes in order */
+        unsigned acc = 0, mm = vmask;
+        while (mm) {
+          int l = __ffs(mm) - 1;
+          mm &= mm - 1;
+          unsigned v = __shfl_sync(vmask, need[r], l);
+          if ((unsigned)l <= lane) acc += v;
+        }
+        x = acc;
+      }
+      excl[r] = running + x - need[r];
+      unsigned last = 31 - __clz(vmask);
+      running += __shfl_sync(vmask, x, last);
+    }
+    const unsigned total = running;
+    const unsigned m = (total + ppc - 1) >> ppc_log;
+    /* 3. chunks for the batch */
+    chunk_range cr{0, 0, 0, 0};
+    if ((int)lane == owner) {
+      cr = take_chunks(h, m);
+      if (cr.k1 + cr.k2) stat_add(h, c, OURO_ST_CARVE, cr.k1 + cr.k2);
+    }
+    cr.p0 = __shfl_sync(vmask, cr.p0, owner);
+    cr.b0 = __shfl_sync(vmask, cr.b0, owner);
+    cr.k1 = __shfl_sync(vmask, cr.k1, owner);
+    cr.k2 = __shfl_sync(vmask, cr.k2, owner);
+    const unsigned g = cr.k1 + cr.k2;
+    for (unsigned k = rk; k < g; k += nl) {
+      const unsigned x = range_chunk(h, cr, k);
+      h.chunk_cls[x] = (unsigned char)c;
+      h.chunk_free[x] = (int)ppc;
+      unsigned *w = h.bits + (size_t)x * h.words_per_chunk;
+      for (unsigned j = 0; j < words_c; ++j) w[j] = ppc >= 32 ? 0xffffffffu : ((1u << ppc) - 1);
+    }
+    __threadfence();
+    __syncwarp(vmask);
+    /* 4. reservations: position i takes min(need, room left in its chunk) */
+    unsigned item[8];
+    for (int r = 0; r < 8; ++r) {
+      item[r] = 0xffffffffu;
+      const unsigned i = rk + (unsigned)r * nl;
+      if (i >= D) continue;
+      const unsigned k = excl[r] >> ppc_log;
+      if (k >= g) continue;                                /* heap exhausted: null answer */
+      const unsigned x = range_chunk(h, cr, k);
+      const unsigned res = min(need[r], ppc - (excl[r] & (ppc - 1)));
+      atomicSub(&h.chunk_free[x], (int)res);
+      item[r] = OURO_CQ_RES | ((res - 1) << 26) | x;
+    }
+    __threadfence();
+    __syncwarp(vmask);
+    /* 5. publish; then queue every new chunk that still has free pages */
+    for (int r = 0; r < 8; ++r) {
+      const unsigned i = rk + (unsigned)r * nl;
+      if (i >= D || !cell[r]) continue;
+      const bool isnull = item[r] == 0xffffffffu;
+      int rc = put_at(h, cell[r], t + i, isnull ? 0 : item[r], isnull);
+      if (VL) vl_event(h, c, cell[r], 1);
+      if (rc == 1 && !isnull) {   /* its group gave up: hand the reserved pages back */
+        const unsigned x = OURO_CQ_ID(item[r]);
+        int before = atomicAdd(&h.chunk_free[x], (int)OURO_CQ_CNT(item[r]));
+        if (before <= 0 && before + (int)OURO_CQ_CNT(item[r]) >= 1) chunk_push<VL>(h, c, x);
+      }
+      if (isnull) stat_add(h, c, OURO_ST_DEAD, 1);
+    }
+    __syncwarp(vmask);
+    for (unsigned k = rk; k < g; k += nl) {
+      const unsigned x = range_chunk(h, cr, k);
+      if (*(volatile int *)&h.chunk_free[x] > 0) chunk_push<VL>(h, c, x);
+    }
+    __syncwarp(vmask);
+    if (g < m) {
+      /* exhausted: every remaining waiting position gets the null answer */
+      unsigned long long dt = 0, dn = 0;
+      if ((int)lane == owner) {
+        for (unsigned it = 0; it < h.spin_limit; ++it) {
+          unsigned long long t2 = ld_acq(&q->tail.v), h2 = ld_acq(&q->head.v);
+          if (h2 <= t2) break;
+          if (VL) vl_slot(h, c, h2 - 1, true);
+          if (atomicCAS(&q->tail.v, t2, h2) == t2) { dt = t2; dn = h2 - t2; break; }
+        }
+        stat_add(h, c, OURO_ST_DEAD, dn);
+      }
+      dt = __shfl_sync(vmask, dt, owner);
+      dn = __shfl_sync(vmask, dn, owner);
+      for (unsigned long long i = rk; i < dn; i += nl) {
+        unsigned long long *cl = slot_at<VL>(h, c, dt + i, true);
+        if (!cl) continue;
+        put_at(h, cl, dt + i, 0, true);
+        if (VL) vl_event(h, c, cl, 1);
+      }
+      break;
+    }
+  }
+  __syncwarp(vmask);
+  if ((int)lane == owner) unlock(&q->lock.v);
+}
+
+/* Claim `got` free pages of chunk x for the lanes of group gmask whose rank
+ * is below got; lanes receive their page index.  The leader claims several
+ * bits per atomicAnd; every lane of gmask calls. */
+__device__ inline unsigned claim_pages(const ouro_heap_dev &h, unsigned x, unsigned ppc, unsigned got,
+                                       unsigned gmask, unsigned leader, unsigned rank, unsigned seed) {
+  const unsigned lane = laneid();
+  const unsigned words_c = (ppc + 31) >> 5;
+  unsigned *bw = h.bits + (size_t)x * h.words_per_chunk;
+  unsigned need = got, base = 0, mine = OURO_NIL;
+  unsigned w = words_c > 1 ? seed % words_c : 0;
+  for (unsigned it = 0; need && it < 4 * words_c + 64; ++it) {
+    unsigned claimed = 0;
+    if (lane == leader) {
+      unsigned v = *(volatile unsigned *)&bw[w];
+      if (v) {
+        unsigned m = 0, tmp = v;
+        for (unsigned k = 0; k < need && tmp; ++k) {
+          unsigned b = tmp & (0u - tmp);
+          m |= b;
+          tmp ^= b;
+        }
+        claimed = atomicAnd(&bw[w], ~m) & m;
+      }
+    }
+    claimed = __shfl_sync(gmask, claimed, leader);
+    const unsigned n = __popc(claimed);
+    if (rank >= base && rank < base + n && rank < got) {
+      unsigned tmp = claimed;
+      for (unsigned k = base; k < rank; ++k) tmp &= tmp - 1;
+      mine = (w << 5) + (__ffs(tmp) - 1);
+    }
+    base += n;
+    need -= n;
+    if (!claimed || need) w = (w + 1 == words_c) ? 0 : w + 1;
+  }
+  if (need && lane == leader) set_error(h, OURO_ERR_TIMEOUT);
+  return mine;
+}
+
+template <int V>
+__device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
+  constexpr bool VL = (V == OURO_CHUNK_VLIST);
+  ouro_qhdr *q = qh(h, cls);
+  const unsigned lane = laneid();
+  const unsigned ppc_log = h.log2_chunk - 4 - cls;
+  const unsigned ppc = 1u << ppc_log;
+  int st = 0;                    /* 0 waiting, 1 page, 2 null */
+  unsigned page = 0, chunk = 0;
+  /* group-leader state: one queue position at a time */
+  bool have = false, posted = false;
+  unsigned long long pos = 0;
+  unsigned long long *cell = nullptr;
+  unsigned ns = h.backoff_min_ns;
+  for (unsigned it = 0;; ++it) {
+    const unsigned pend = __ballot_sync(vmask, st == 0);
+    if (!pend) break;
+    const unsigned gmask = __match_any_sync(vmask, st == 0 ? cls : -1) & pend;
+    const bool mine = st == 0;
+    const unsigned leader = mine ? __ffs(gmask) - 1 : 0;
+    const unsigned rank = mine ? __popc(gmask & lanemask_lt()) : 0;
+    const unsigned need = __popc(gmask);
+    unsigned got_item = 0, res = 0;    /* res: 0 none, 1 chunk, 2 null marker */
+    bool debt = false;
+    if (mine && lane == leader) {
+      if (!have) {
+        pos = atomicAdd(&q->head.v, 1ull);
+        have = true;
+        posted = false;
+        cell = nullptr;
+      }
+      if (!cell) cell = slot_at<VL>(h, cls, pos, false);
+      unsigned item = 0;
+      int r = cell ? try_take<VL>(h, cls, cell, pos, &item) : 0;
+      if (r) {
+        if (VL) vl_event(h, cls, cell, 1);
+        have = false;
+        res = (unsigned)r;
+        got_item = item;
+      } else if (pos >= ld_acq(&q->tail.v)) {
+        debt = true;
+        if (!posted) {
+          if (!cell && VL) cell = vl_slot(h, cls, pos, true);
+          if (cell) {
+            const unsigned long long e = slot(pos, 0);
+            posted = true;
+            cas_ar(cell, e, slot(pos, need));
+          }
+        }
+      }
+      if (it >= h.spin_limit && !res) {                 /* bounded wait ran out */
+        if (!cell) cell = slot_at<VL>(h, cls, pos, true);
+        unsigned item2 = 0;
+        int g = cell ? give_up<VL>(h, cls, cell, pos, &item2) : 0;
+        if (g == 1 || g == 2) {
+          res = (unsigned)g;
+          got_item = item2;
+        } else {
+          res = 2;
+          set_error(h, OURO_ERR_TIMEOUT);
+          stat_add(h, cls, OURO_ST_CANCEL, 1);
+        }
+        if (VL && cell && g) vl_event(h, cls, cell, 1);
+        have = false;
+      }
+    }
+    /* carve: one lock taker per class among the debtors of the warp */
+    const unsigned dmask = __ballot_sync(vmask, debt);
+    if (dmask) {
+      const bool got = debt && try_lock(&q->lock.v);
+      unsigned lockers = __ballot_sync(vmask, got);
+      while (lockers) {
+        const int j = __ffs(lockers) - 1;
+        lockers &= lockers - 1;
+        chunk_carve<V>(h, __shfl_sync(vmask, cls, j), vmask, j);
+      }
+    }
+    /* every group learns its leader's answer */
+    const unsigned gl_leader = mine ? leader : lane;
+    res = __shfl_sync(vmask, res, gl_leader);
+    got_item = __shfl_sync(vmask, got_item, gl_leader);
+    const unsigned any = __ballot_sync(vmask, mine && res != 0);
+    if (mine && res == 2) st = 2;
+    /* groups holding a chunk: reserve and claim pages (all lanes of vmask take part) */
+    unsigned work = any;
+    while (work) {
+      const int j = __ffs(work) - 1;
+      const unsigned jg = __shfl_sync(vmask, gmask, j);
+      work &= ~jg;
+      const unsigned jres = __shfl_sync(vmask, res, j);
+      if (jres != 1) continue;
+      const unsigned jitem = __shfl_sync(vmask, got_item, j);
+      const unsigned jneed = __popc(jg);
+      const unsigned jleader = __ffs(jg) - 1;
+      const int jcls = __shfl_sync(vmask, cls, j);
+      const unsigned jppc = 1u << (h.log2_chunk - 4 - jcls);
+      const unsigned x = OURO_CQ_ID(jitem);
+      unsigned granted = 0;
+      if (lane == jleader) {
+        if (jitem & OURO_CQ_RES) {
+          granted = min(OURO_CQ_CNT(jitem), jneed);
+        } else {
+          const int old = atomicSub(&h.chunk_free[x], (int)jneed);
+          granted = old <= 0 ? 0 : min((unsigned)old, jneed);
+          const int left = old - (int)jneed;
+          if (left >= 1) chunk_push<(V == OURO_CHUNK_VLIST)>(h, jcls, x);
+          if (granted < jneed) {
+            const int ex = (int)(jneed - granted);
+            const int b = atomicAdd(&h.chunk_free[x], ex);
+            if (b <= 0 && b + ex >= 1) chunk_push<(V == OURO_CHUNK_VLIST)>(h, jcls, x);
+          }
+        }
+      }
+      granted = __shfl_sync(vmask, granted, jleader);
+      const bool in_g = (jg >> lane) & 1;
+      const unsigned jrank = __popc(jg & lanemask_lt());
+      unsigned pg = OURO_NIL;
+      if (in_g) pg = claim_pages(h, x, jppc, granted, jg, jleader, jrank, (smid() << 8) ^ x ^ (unsigned)it);
+      if (in_g && pg != OURO_NIL) {
+        st = 1;
+        page = pg;
+        chunk = x;
+      }
+    }
+    if (__ballot_sync(vmask, st == 0) == 0) break;
+    if (!any) {
+      __nanosleep(ns);
+      ns = min(ns * 2, h.backoff_max_ns);
+    } else {
+      ns = h.backoff_min_ns;
+    }
+  }
+  void *ret = nullptr;
+  if (st == 1) ret = h.base + ((size_t)chunk << h.log2_chunk) + ((size_t)page << (4 + cls));
+  const unsigned g2 = __match_any_sync(vmask, cls);
+  const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
+  if (lane == (unsigned)(__ffs(g2) - 1)) {
+    stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
+    stat_add(h, cls, OURO_ST_FAILED, __popc(g2) - __popc(okm));
+  }
+  (void)ppc;
+  return ret;
+}
+
+/* free into a chunk queue: every lane of mask calls; lanes with cls < 0 only take part */
+template <int V>
+__device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, unsigned mask) {
+  constexpr bool VL = (V == OURO_CHUNK_VLIST);
+  const unsigned lane = laneid();
+  unsigned x = 0, pg = 0;
+  if (cls >= 0) {
+    const unsigned long long off = (unsigned long long)((const unsigned char *)p - h.base);
+    x = (unsigned)(off >> h.log2_chunk);
+    pg = (unsigned)((off & (h.chunk_bytes - 1)) >> (4 + cls));
+  }
+  /* 1. set the page bits, one atomicOr per (chunk, word) group */
+  __threadfence();
+  const unsigned long long wkey = cls >= 0 ? (((unsigned long long)x << 32) | (pg >> 5)) : ~0ull;
+  const unsigned wg = __match_any_sync(mask, wkey);
+  const unsigned bit = cls >= 0 ? 1u << (pg & 31) : 0u;
+  const unsigned bits = __reduce_or_sync(wg, bit);
+  unsigned old = 0;
+  if (cls >= 0 && lane == (unsigned)(__ffs(wg) - 1))
+    old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bits);
+  old = __shfl_sync(mask, old, __ffs(wg) - 1);
+  if (cls >= 0 && (old & bit)) {
+    set_error(h, OURO_ERR_DOUBLE_FREE);
+    cls = -1;
+  }
+  /* 2. count the pages back per chunk; lifting the count from <= 0 queues it */
+  const unsigned cg = __match_any_sync(mask, cls >= 0 ? x : OURO_NIL) & __ballot_sync(mask, cls >= 0);
+  if (cls >= 0 && lane == (unsigned)(__ffs(cg) - 1)) {
+    const int k = __popc(cg);
+    __threadfence();
+    const int b = atomicAdd(&h.chunk_free[x], k);
+    if (b <= 0 && b + k >= 1) chunk_push<VL>(h, cls, x);
+  }
+  const unsigned sg = __match_any_sync(mask, cls);
+  if (cls >= 0 && lane == (unsigned)(__ffs(sg) - 1)) stat_add(h, cls, OURO_ST_FREE, __popc(sg));
+}
+
 }  // namespace detail
 }  // namespace ouro
 
@@ -711,6 +1103,8 @@ static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t 
   switch (h.variant) {
     case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, vmask);
     case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, vmask);
+    case OURO_CHUNK_ARRAY: return chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, vmask);
+    case OURO_CHUNK_VLIST: return chunk_malloc<OURO_CHUNK_VLIST>(h, cls, vmask);
     default: return nullptr;
   }
 }
@@ -725,7 +1119,7 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
   if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE);
-    else if (h.checked) {
+    else if (h.checked && (h.variant == OURO_PAGE_ARRAY || h.variant == OURO_PAGE_VLIST)) {
       unsigned ppcm = (1u << (h.log2_chunk - 4 - cls)) - 1;
       unsigned pg = item & ppcm, x = item >> (h.log2_chunk - 4 - cls);
       unsigned bit = 1u << (pg & 31);
@@ -734,6 +1128,8 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
       if (old & bit) { set_error(h, OURO_ERR_DOUBLE_FREE); cls = -1; }
     }
   }
+  if (h.variant == OURO_CHUNK_ARRAY) { chunk_free_impl<OURO_CHUNK_ARRAY>(h, cls, p, mask); return; }
+  if (h.variant == OURO_CHUNK_VLIST) { chunk_free_impl<OURO_CHUNK_VLIST>(h, cls, p, mask); return; }
   const unsigned vmask = __ballot_sync(mask, cls >= 0);
   if (cls < 0) return;
   switch (h.variant) {

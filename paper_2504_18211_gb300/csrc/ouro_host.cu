@@ -118,7 +118,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
       variant != OURO_CHUNK_VLIST)
     return OURO_EINVAL;
   if (d_heap_buf && ((uintptr_t)d_heap_buf & 255)) return OURO_EINVAL;
-  if (!is_page(variant)) return OURO_ENOTSUP;   /* chunk queues: see ouro_chunk.cuh when enabled */
+  if (!is_page(variant) && bytes / chunk_bytes > (1ull << 26)) return OURO_EINVAL;   /* chunk id field: 26 bits */
 
   ouro_options o;
   o.spin_limit = 1u << 20;
@@ -280,7 +280,8 @@ __global__ void k_collect_queue(ouro_heap_dev h, int c, unsigned *out, unsigned 
     if (!cell) continue;
     unsigned long long v = *cell;
     if (slot_d(v, p) != 1) continue;
-    if (n < cap) out[n] = lo32(v);
+    const bool cq = h.variant == OURO_CHUNK_ARRAY || h.variant == OURO_CHUNK_VLIST;
+    if (n < cap) out[n] = cq ? OURO_CQ_ID(lo32(v)) : lo32(v);
     n++;
   }
   *n_out = n;
@@ -438,6 +439,7 @@ extern "C" void ouro_snapshot_free(ouro_snapshot *sn) {
 /* -------------------------------------------------------------------- trim */
 /* 1. count the queued pages of every chunk (page queues) */
 __global__ void k_trim_count(ouro_heap_dev h, unsigned *qcount) {
+  if (h.variant == OURO_CHUNK_ARRAY || h.variant == OURO_CHUNK_VLIST) return;   /* counts live in chunk_free */
   const int c = blockIdx.y;
   ouro_qhdr *q = qh(h, c);
   const unsigned long long hd = q->head.v, tl = q->tail.v;
@@ -461,9 +463,11 @@ __global__ void k_trim_mark(ouro_heap_dev h, const unsigned *qcount, unsigned ch
     unsigned char ip = 0;
     if (c < h.n_classes) {
       unsigned long long ppc = 1ull << (h.log2_chunk - 4 - c);
-      if (qcount[x] == ppc) {
+      const unsigned long long free_pages = h.chunk_free ? (unsigned long long)max(h.chunk_free[x], 0) : qcount[x];
+      if (free_pages == ppc) {
         h.chunk_cls[x] = OURO_CLS_NONE;
         ip = 1;
+        if (h.chunk_free) h.chunk_free[x] = 0;
         if (h.bits)
           for (unsigned w = 0; w < h.words_per_chunk; ++w) h.bits[x * h.words_per_chunk + w] = 0;
       }
@@ -490,7 +494,8 @@ __global__ void k_trim_compact(ouro_heap_dev h, int c, const unsigned char *in_p
   ouro_qhdr *q = qh(h, c);
   const unsigned long long hd = q->head.v, tl = q->tail.v;
   const unsigned ppc_log = h.log2_chunk - 4 - c;
-  const bool vl = h.variant == OURO_PAGE_VLIST;
+  const bool vl = h.variant == OURO_PAGE_VLIST || h.variant == OURO_CHUNK_VLIST;
+  const bool cq = h.variant == OURO_CHUNK_ARRAY || h.variant == OURO_CHUNK_VLIST;
   __shared__ unsigned warp_tot[32];
   __shared__ unsigned long long base;
   if (threadIdx.x == 0) base = 0;
@@ -506,7 +511,8 @@ __global__ void k_trim_compact(ouro_heap_dev h, int c, const unsigned char *in_p
         unsigned long long v = *cell;
         if (slot_d(v, p) == 1) {
           item = lo32(v);
-          keep = !in_pool[item >> ppc_log];
+          keep = !in_pool[cq ? OURO_CQ_ID(item) : item >> ppc_log];
+          if (cq) item = OURO_CQ_ID(item);
         }
       }
     }
@@ -633,7 +639,6 @@ __global__ void k_trim_relay_list(ouro_heap_dev h, int c, const unsigned *tmp, c
 
 extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   if (!H) return OURO_EINVAL;
-  if (!is_page(H->d.variant)) return OURO_ENOTSUP;
   cudaStream_t s = S(stream);
   const ouro_heap_dev &d = H->d;
   OURO_CUDA(cudaStreamSynchronize(s));
@@ -674,7 +679,7 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   OURO_LAUNCHED();
   for (unsigned c = 0; c < d.n_classes; ++c) {
     const unsigned *src = (const unsigned *)tmp.p + (size_t)c * span_max;
-    if (d.variant == OURO_PAGE_ARRAY) {
+    if (d.variant == OURO_PAGE_ARRAY || d.variant == OURO_CHUNK_ARRAY) {
       k_trim_relay_ring<<<grid, 256, 0, s>>>(d, (int)c, src, ncount + c);
       OURO_LAUNCHED();
       k_trim_reset_q<<<1, 1, 0, s>>>(d, (int)c, ncount + c);

@@ -26,7 +26,8 @@ __device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long 
     stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
     return nullptr;
   }
-  return page_malloc<V>(h, cls, vmask);
+  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) return page_malloc<V>(h, cls, vmask);
+  else return chunk_malloc<V>(h, cls, vmask);
 }
 
 template <int V>
@@ -37,7 +38,7 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
   if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE);
-    else if (h.checked) {
+    else if (h.checked && (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST)) {
       const unsigned sh = h.log2_chunk - 4 - cls;
       const unsigned pg = item & ((1u << sh) - 1), x = item >> sh, bit = 1u << (pg & 31);
       __threadfence();
@@ -48,9 +49,13 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
       }
     }
   }
-  const unsigned vmask = __ballot_sync(mask, cls >= 0);
-  if (cls < 0) return;
-  page_free<V>(h, cls, item, vmask);
+  if constexpr (V == OURO_CHUNK_ARRAY || V == OURO_CHUNK_VLIST) {
+    chunk_free_impl<V>(h, cls, p, mask);
+  } else {
+    const unsigned vmask = __ballot_sync(mask, cls >= 0);
+    if (cls < 0) return;
+    page_free<V>(h, cls, item, vmask);
+  }
 }
 
 /* ------------------------------------------------------------ batch API */
@@ -280,24 +285,22 @@ inline int grid_for(size_t n, int block, int cap) {
 }  // namespace
 
 /* ------------------------------------------------------------- C entries */
+#define OURO_DISPATCH(VAR, CALL)                                   \
+  switch (VAR) {                                                   \
+    case OURO_PAGE_ARRAY: { constexpr int V = OURO_PAGE_ARRAY; CALL; break; }   \
+    case OURO_PAGE_VLIST: { constexpr int V = OURO_PAGE_VLIST; CALL; break; }   \
+    case OURO_CHUNK_ARRAY: { constexpr int V = OURO_CHUNK_ARRAY; CALL; break; } \
+    case OURO_CHUNK_VLIST: { constexpr int V = OURO_CHUNK_VLIST; CALL; break; } \
+    default: return OURO_ENOTSUP;                                  \
+  }
+
 extern "C" ouro_status ouro_batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n,
                                          void *stream) {
   if (!H || (n && (!d_sizes || !d_ptrs))) return OURO_EINVAL;
   if (!n) return OURO_OK;
   const int block = 256;
-  switch (H->d.variant) {
-    case OURO_PAGE_ARRAY: {
-      int g = grid_for(n, block, 1 << 20);
-      k_batch_malloc<OURO_PAGE_ARRAY><<<g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n);
-      break;
-    }
-    case OURO_PAGE_VLIST: {
-      int g = grid_for(n, block, 1 << 20);
-      k_batch_malloc<OURO_PAGE_VLIST><<<g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n);
-      break;
-    }
-    default: return OURO_ENOTSUP;
-  }
+  const int g = grid_for(n, block, 1 << 20);
+  OURO_DISPATCH(H->d.variant, (k_batch_malloc<V><<<g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n)));
   OURO_LAUNCHED();
   return OURO_OK;
 }
@@ -307,11 +310,7 @@ extern "C" ouro_status ouro_batch_free(ouro_heap *H, void *const *d_ptrs, size_t
   if (!n) return OURO_OK;
   const int block = 256;
   const int g = grid_for(n, block, 1 << 20);
-  switch (H->d.variant) {
-    case OURO_PAGE_ARRAY: k_batch_free<OURO_PAGE_ARRAY><<<g, block, 0, S(stream)>>>(H->d, d_ptrs, n); break;
-    case OURO_PAGE_VLIST: k_batch_free<OURO_PAGE_VLIST><<<g, block, 0, S(stream)>>>(H->d, d_ptrs, n); break;
-    default: return OURO_ENOTSUP;
-  }
+  OURO_DISPATCH(H->d.variant, (k_batch_free<V><<<g, block, 0, S(stream)>>>(H->d, d_ptrs, n)));
   OURO_LAUNCHED();
   return OURO_OK;
 }
@@ -348,19 +347,8 @@ extern "C" ouro_status ouro_round_fused(ouro_heap *H, const uint32_t *d_sizes, s
   OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
   if (!n) return OURO_OK;
   const int block = 256;
-  switch (H->d.variant) {
-    case OURO_PAGE_ARRAY: {
-      int g = grid_for(n, block, occupancy_grid(k_round_fused<OURO_PAGE_ARRAY>, block));
-      k_round_fused<OURO_PAGE_ARRAY><<<g, block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs);
-      break;
-    }
-    case OURO_PAGE_VLIST: {
-      int g = grid_for(n, block, occupancy_grid(k_round_fused<OURO_PAGE_VLIST>, block));
-      k_round_fused<OURO_PAGE_VLIST><<<g, block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs);
-      break;
-    }
-    default: return OURO_ENOTSUP;
-  }
+  OURO_DISPATCH(H->d.variant, (k_round_fused<V><<<grid_for(n, block, occupancy_grid(k_round_fused<V>, block)),
+                                                 block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs)));
   OURO_LAUNCHED();
   return OURO_OK;
 }

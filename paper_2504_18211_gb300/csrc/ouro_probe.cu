@@ -63,7 +63,8 @@ __global__ void k_malloc_timed(ouro_heap_dev h, const uint32_t *sizes, void **pt
       const unsigned mask = __activemask();
       const int cls = size_class(h, sizes[i]);
       const unsigned vmask = __ballot_sync(mask, cls >= 0);
-      p = cls >= 0 ? page_malloc<V>(h, cls, vmask) : nullptr;
+      if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) p = cls >= 0 ? page_malloc<V>(h, cls, vmask) : nullptr;
+      else p = cls >= 0 ? chunk_malloc<V>(h, cls, vmask) : nullptr;
     }
     const unsigned long long t1 = clock64();
     ptrs[i] = p;
@@ -97,6 +98,8 @@ extern "C" ouro_status ouro_malloc_latency(ouro_heap *H, const uint32_t *d_sizes
   switch (H->d.variant) {
     case OURO_PAGE_ARRAY: k_malloc_timed<OURO_PAGE_ARRAY><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
     case OURO_PAGE_VLIST: k_malloc_timed<OURO_PAGE_VLIST><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
+    case OURO_CHUNK_ARRAY: k_malloc_timed<OURO_CHUNK_ARRAY><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
+    case OURO_CHUNK_VLIST: k_malloc_timed<OURO_CHUNK_VLIST><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
     default: return OURO_ENOTSUP;
   }
   OURO_LAUNCHED();
