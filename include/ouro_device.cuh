@@ -1004,7 +1004,13 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       unsigned granted = 0;
       if (lane == jleader) {
         if (jitem & OURO_CQ_RES) {
-          granted = min(OURO_CQ_CNT(jitem), jneed);
+          const unsigned cnt = OURO_CQ_CNT(jitem);
+          granted = min(cnt, jneed);
+          if (cnt > jneed) {   /* reserved for a warp-sized need that was not posted: hand back the rest */
+            const int ex = (int)(cnt - jneed);
+            const int b = atomicAdd(&h.chunk_free[x], ex);
+            if (b <= 0 && b + ex >= 1) chunk_push<(V == OURO_CHUNK_VLIST)>(h, jcls, x);
+          }
         } else {
           const int old = atomicSub(&h.chunk_free[x], (int)jneed);
           granted = old <= 0 ? 0 : min((unsigned)old, jneed);
