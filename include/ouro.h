@@ -110,6 +110,8 @@ typedef struct {
   uint64_t zero_reqs, too_large;          /* requests of 0 bytes / above one chunk */
   uint64_t bump, pool_size, seg_chunks, spare_chunks;
   uint32_t error_bits, n_classes;
+  uint32_t error_site;                    /* where the first error was recorded (device header's OURO_SITE_*) */
+  uint32_t reserved;
 } ouro_stats;
 
 /* Host copy of the queue state, for tests (ouro_heap_snapshot).  Arrays are

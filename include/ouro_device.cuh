@@ -77,7 +77,7 @@ struct ouro_glob {
   ouro_line pool_taken;  /* pool entries handed out (may overshoot pool_size) */
   unsigned long long pool_size;
   unsigned int error_bits;
-  unsigned int pad;
+  unsigned int error_site;   /* OURO_SITE_* of the first error */
 };
 
 /* header of a virtualized-list segment (first 64 bytes of its chunk) */
@@ -155,8 +155,16 @@ __device__ __forceinline__ void stat_add(const ouro_heap_dev &h, int row, int ki
   if (v)
     atomicAdd(&h.stats[((size_t)row * OURO_NSTAT + kind) * OURO_SHARDS + (smid() & (OURO_SHARDS - 1))], v);
 }
-__device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits) {
+/* error sites: where the first recorded error of a heap came from */
+enum {
+  OURO_SITE_SPARE = 1, OURO_SITE_VL_FIRST, OURO_SITE_VL_NEXT, OURO_SITE_VL_WALK, OURO_SITE_PUT,
+  OURO_SITE_PUSH_ONE, OURO_SITE_PAGE_GIVEUP, OURO_SITE_PAGE_CHECKED, OURO_SITE_CLAIM,
+  OURO_SITE_CHUNK_GIVEUP, OURO_SITE_CHUNK_DOUBLE, OURO_SITE_BAD_FREE, OURO_SITE_PAGE_DOUBLE,
+  OURO_SITE_TRIM
+};
+__device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits, unsigned site) {
   atomicOr(&gl(h)->error_bits, bits);
+  atomicCAS(&gl(h)->error_site, 0u, site);
 }
 
 /* power-of-two class: ceil(log2 n) - 4, floor 16 B; -1 for 0 or above one chunk */
@@ -242,7 +250,7 @@ __device__ inline void spare_push(const ouro_heap_dev &h, int c, unsigned x) {
     __threadfence();
     if (cas_ar(top, old, pack(hi32(old) + 1, x)) == old) return;
   }
-  set_error(h, OURO_ERR_TIMEOUT);
+  set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_SPARE);
 }
 __device__ inline unsigned spare_pop(const ouro_heap_dev &h, int c) {
   unsigned long long *top = &qh(h, c)->spare.v;
@@ -335,7 +343,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
           unsigned x = seg_new(h, c, hi32(cur));
           if (x == OURO_NIL) {
             st_rel(&q->back.v, cur);
-            set_error(h, OURO_ERR_QUEUE_FULL);
+            set_error(h, OURO_ERR_QUEUE_FULL, OURO_SITE_VL_FIRST);
             return nullptr;
           }
           st_rel(&q->front.v, pack(hi32(cur), x));
@@ -368,7 +376,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
         unsigned x = seg_new(h, c, hi32(cur) + 1);
         if (x == OURO_NIL) {
           st_rel(&sg->link, link);
-          set_error(h, OURO_ERR_QUEUE_FULL);
+          set_error(h, OURO_ERR_QUEUE_FULL, OURO_SITE_VL_NEXT);
           return nullptr;
         }
         st_rel(&sg->link, pack(hi32(cur), x));
@@ -387,7 +395,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
     }
     cur = pack(hi32(cur) + 1, nxt);
   }
-  set_error(h, OURO_ERR_TIMEOUT);
+  set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_VL_WALK);
   return nullptr;
 }
 
@@ -418,7 +426,7 @@ __device__ inline int put_at(const ouro_heap_dev &h, unsigned long long *cell, u
     ns = min(ns * 2, h.backoff_max_ns);
     expect = slot(pos, 0);
   }
-  set_error(h, OURO_ERR_QUEUE_OVERFLOW);
+  set_error(h, OURO_ERR_QUEUE_OVERFLOW, OURO_SITE_PUT);
   return -1;
 }
 
@@ -472,7 +480,7 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
     if (rc < 0) return;
     stat_add(h, c, OURO_ST_REPUSH, 1);
   }
-  set_error(h, OURO_ERR_TIMEOUT);
+  set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_PUSH_ONE);
 }
 
 /* ---------------------------------------------- page queues: carve batch */
@@ -620,7 +628,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
           int g = cell ? give_up<VL>(h, cls, cell, pos, &item) : 0;
           st = g ? g : 3;
           if (st == 3) {
-            set_error(h, OURO_ERR_TIMEOUT);
+            set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_PAGE_GIVEUP);
             stat_add(h, cls, OURO_ST_CANCEL, 1);
           }
         }
@@ -643,7 +651,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       unsigned x = item >> (h.log2_chunk - 4 - cls);
       unsigned bit = 1u << (pg & 31);
       unsigned old = atomicAnd(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], ~bit);
-      if (!(old & bit)) set_error(h, OURO_ERR_DOUBLE_FREE);
+      if (!(old & bit)) set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_CHECKED);
     }
     res = h.base + ((size_t)item << (4 + cls));
   }
@@ -797,7 +805,7 @@ __device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int o
     for (unsigned k = rk; k < g; k += nl) {
       const unsigned x = range_chunk(h, cr, k);
       h.chunk_cls[x] = (unsigned char)c;
-      h.chunk_free[x] = (int)ppc;
+      h.chunk_free[x] = 0;                 /* reservations below, then +ppc once published */
       unsigned *w = h.bits + (size_t)x * h.words_per_chunk;
       for (unsigned j = 0; j < words_c; ++j) w[j] = ppc >= 32 ? 0xffffffffu : ((1u << ppc) - 1);
     }
@@ -833,9 +841,13 @@ __device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int o
       if (isnull) stat_add(h, c, OURO_ST_DEAD, 1);
     }
     __syncwarp(vmask);
+    /* the count stays <= 0 until now (frees of reserved pages only return
+     * what was reserved), so adding the pages here lifts it above zero
+     * exactly once: the chunk is queued once iff it has a free page */
     for (unsigned k = rk; k < g; k += nl) {
       const unsigned x = range_chunk(h, cr, k);
-      if (*(volatile int *)&h.chunk_free[x] > 0) chunk_push<VL>(h, c, x);
+      const int b = atomicAdd(&h.chunk_free[x], (int)ppc);
+      if (b <= 0 && b + (int)ppc >= 1) chunk_push<VL>(h, c, x);
     }
     __syncwarp(vmask);
     if (g < m) {
@@ -866,8 +878,11 @@ __device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int o
 }
 
 /* Claim `got` free pages of chunk x for the lanes of group gmask whose rank
- * is below got; lanes receive their page index.  The leader claims several
- * bits per atomicAnd; every lane of gmask calls. */
+ * is below got; lanes receive their page index.  The reservation on the
+ * chunk's count guarantees that enough bits are set, so the claim keeps
+ * scanning (bounded by spin_limit) until it has them all.  The leader
+ * claims several bits per atomicAnd and reuses the word value the atomic
+ * returned; every lane of gmask calls. */
 __device__ inline unsigned claim_pages(const ouro_heap_dev &h, unsigned x, unsigned ppc, unsigned got,
                                        unsigned gmask, unsigned leader, unsigned rank, unsigned seed) {
   const unsigned lane = laneid();
@@ -875,32 +890,46 @@ __device__ inline unsigned claim_pages(const ouro_heap_dev &h, unsigned x, unsig
   unsigned *bw = h.bits + (size_t)x * h.words_per_chunk;
   unsigned need = got, base = 0, mine = OURO_NIL;
   unsigned w = words_c > 1 ? seed % words_c : 0;
-  for (unsigned it = 0; need && it < 4 * words_c + 64; ++it) {
-    unsigned claimed = 0;
+  unsigned v = 0, empty = 0, ns = h.backoff_min_ns;
+  if (lane == leader) v = *(volatile unsigned *)&bw[w];
+  for (unsigned it = 0; need && it < h.spin_limit; ++it) {
+    unsigned claimed = 0, cword = 0;
     if (lane == leader) {
-      unsigned v = *(volatile unsigned *)&bw[w];
       if (v) {
+        cword = w;
         unsigned m = 0, tmp = v;
         for (unsigned k = 0; k < need && tmp; ++k) {
-          unsigned b = tmp & (0u - tmp);
+          const unsigned b = tmp & (0u - tmp);
           m |= b;
           tmp ^= b;
         }
-        claimed = atomicAnd(&bw[w], ~m) & m;
+        const unsigned old = atomicAnd(&bw[w], ~m);
+        claimed = old & m;
+        v = old & ~m;                       /* bits still free in this word */
+        empty = 0;
+      }
+      if (!v) {
+        w = (w + 1 == words_c) ? 0 : w + 1;
+        if (++empty > words_c) {            /* a whole pass found nothing: bits still being freed */
+          __nanosleep(ns);
+          ns = min(ns * 2, h.backoff_max_ns);
+          empty = 0;
+        }
+        v = *(volatile unsigned *)&bw[w];
       }
     }
+    const unsigned cw = __shfl_sync(gmask, claimed ? cword : 0u, leader);
     claimed = __shfl_sync(gmask, claimed, leader);
     const unsigned n = __popc(claimed);
     if (rank >= base && rank < base + n && rank < got) {
       unsigned tmp = claimed;
       for (unsigned k = base; k < rank; ++k) tmp &= tmp - 1;
-      mine = (w << 5) + (__ffs(tmp) - 1);
+      mine = (cw << 5) + (__ffs(tmp) - 1);
     }
     base += n;
     need -= n;
-    if (!claimed || need) w = (w + 1 == words_c) ? 0 : w + 1;
   }
-  if (need && lane == leader) set_error(h, OURO_ERR_TIMEOUT);
+  if (need && lane == leader) set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_CLAIM);
   return mine;
 }
 
@@ -963,7 +992,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
           got_item = item2;
         } else {
           res = 2;
-          set_error(h, OURO_ERR_TIMEOUT);
+          set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_CHUNK_GIVEUP);
           stat_add(h, cls, OURO_ST_CANCEL, 1);
         }
         if (VL && cell && g) vl_event(h, cls, cell, 1);
@@ -1027,7 +1056,9 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       const bool in_g = (jg >> lane) & 1;
       const unsigned jrank = __popc(jg & lanemask_lt());
       unsigned pg = OURO_NIL;
-      if (in_g) pg = claim_pages(h, x, jppc, granted, jg, jleader, jrank, (smid() << 8) ^ x ^ (unsigned)it);
+      /* start word: spread groups of different warps over the chunk's words */
+      const unsigned seed = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 0x9E3779B1u ^ (x * 0x85EBCA6Bu) ^ it;
+      if (in_g) pg = claim_pages(h, x, jppc, granted, jg, jleader, jrank, seed >> 7);
       if (in_g && pg != OURO_NIL) {
         st = 1;
         page = pg;
@@ -1076,7 +1107,7 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
     old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bits);
   old = __shfl_sync(mask, old, __ffs(wg) - 1);
   if (cls >= 0 && (old & bit)) {
-    set_error(h, OURO_ERR_DOUBLE_FREE);
+    set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_CHUNK_DOUBLE);
     cls = -1;
   }
   /* 2. count the pages back per chunk; lifting the count from <= 0 queues it */
@@ -1124,14 +1155,14 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
   int cls = -1;
   if (p) {
     cls = locate(h, p, &item);
-    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE);
+    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (h.checked && (h.variant == OURO_PAGE_ARRAY || h.variant == OURO_PAGE_VLIST)) {
       unsigned ppcm = (1u << (h.log2_chunk - 4 - cls)) - 1;
       unsigned pg = item & ppcm, x = item >> (h.log2_chunk - 4 - cls);
       unsigned bit = 1u << (pg & 31);
       __threadfence();
       unsigned old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bit);
-      if (old & bit) { set_error(h, OURO_ERR_DOUBLE_FREE); cls = -1; }
+      if (old & bit) { set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_DOUBLE); cls = -1; }
     }
   }
   if (h.variant == OURO_CHUNK_ARRAY) { chunk_free_impl<OURO_CHUNK_ARRAY>(h, cls, p, mask); return; }

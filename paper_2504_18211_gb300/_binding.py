@@ -53,7 +53,8 @@ class Stats(C.Structure):
                  "repushes", "dead")] + \
                [("zero_reqs", C.c_uint64), ("too_large", C.c_uint64), ("bump", C.c_uint64),
                 ("pool_size", C.c_uint64), ("seg_chunks", C.c_uint64), ("spare_chunks", C.c_uint64),
-                ("error_bits", C.c_uint32), ("n_classes", C.c_uint32)]
+                ("error_bits", C.c_uint32), ("n_classes", C.c_uint32),
+                ("error_site", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class Snapshot(C.Structure):
@@ -158,7 +159,7 @@ def _stats_dict(s: Stats) -> dict:
     out = {k: [int(x) for x in getattr(s, k)[:nc]] for k in
            ("mallocs", "frees", "failed", "carves", "carved_now", "queued", "live", "repushes", "dead")}
     for k in ("zero_reqs", "too_large", "bump", "pool_size", "seg_chunks", "spare_chunks",
-              "error_bits", "n_classes"):
+              "error_bits", "n_classes", "error_site"):
         out[k] = int(getattr(s, k))
     return out
 
@@ -178,7 +179,7 @@ def ouro_heap_stats(h: int, stream=None) -> dict:
     out = {k: [int(x) for x in getattr(s, k)[:nc]] for k in
            ("mallocs", "frees", "failed", "carves", "carved_now", "queued", "live", "repushes", "dead")}
     for k in ("zero_reqs", "too_large", "bump", "pool_size", "seg_chunks", "spare_chunks",
-              "error_bits", "n_classes"):
+              "error_bits", "n_classes", "error_site"):
         out[k] = int(getattr(s, k))
     return out
 

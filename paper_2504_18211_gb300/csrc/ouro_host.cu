@@ -375,6 +375,7 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
   out->bump = g.bump.v < d.n_chunks ? g.bump.v : d.n_chunks;
   out->pool_size = g.pool_taken.v < g.pool_size ? g.pool_size - g.pool_taken.v : 0;
   out->error_bits = g.error_bits;
+  out->error_site = g.error_site;
   return g.error_bits ? OURO_EDEVICE : OURO_OK;
 }
 
@@ -618,7 +619,7 @@ __global__ void k_trim_relay_list(ouro_heap_dev h, int c, const unsigned *tmp, c
         else seg_of(h, prev)->link = pack((unsigned)(s - 1), x);
         q->back.v = pack((unsigned)s, x);
       } else {
-        set_error(h, OURO_ERR_QUEUE_FULL);
+        set_error(h, OURO_ERR_QUEUE_FULL, OURO_SITE_TRIM);
       }
       seg_chunk = x;
     }
@@ -809,5 +810,6 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
   out->bump = g.bump.v < d.n_chunks ? g.bump.v : d.n_chunks;
   out->pool_size = g.pool_taken.v < g.pool_size ? g.pool_size - g.pool_taken.v : 0;
   out->error_bits = g.error_bits;
+  out->error_site = g.error_site;
   return g.error_bits ? OURO_EDEVICE : OURO_OK;
 }

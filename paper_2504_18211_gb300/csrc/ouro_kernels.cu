@@ -37,14 +37,14 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
   int cls = -1;
   if (p) {
     cls = locate(h, p, &item);
-    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE);
+    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (h.checked && (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST)) {
       const unsigned sh = h.log2_chunk - 4 - cls;
       const unsigned pg = item & ((1u << sh) - 1), x = item >> sh, bit = 1u << (pg & 31);
       __threadfence();
       unsigned old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bit);
       if (old & bit) {
-        set_error(h, OURO_ERR_DOUBLE_FREE);
+        set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_DOUBLE);
         cls = -1;
       }
     }

@@ -289,6 +289,7 @@ def test_full_scale_sweep(ouro, variant):
         assert st["mallocs"] == ost["mallocs"] and st["frees"] == ost["frees"]
         out = heap.round_fused(to_dev(sizes), seed, 1)
         assert ouro.check_to_dict(out) == ores
-        assert heap.stats()["error_bits"] == 0
+        st2 = heap.stats()
+        assert st2["error_bits"] == 0, (st2["error_bits"], st2["error_site"])
         heap.trim()
         same_canonical_as_post_create(heap.snapshot(), bytes_ // chunk)
