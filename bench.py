@@ -10,7 +10,7 @@ kernel.  value = malloc+free operations per second over the timed steps
 
 Printed on one JSON line, besides the contract keys: the per-launch form
 (malloc / write / check / free kernels, whose malloc+free share is the
-paper's own timing), the virtualized-list variant, the malloc latency
+paper's own timing), the other three queue variants, the malloc latency
 histogram (p50/p99), the measured L2 atomic rates and the allocator's
 fraction of them, the end-to-end figure with host buffers, and the CPU
 oracle on a bounded sample.
@@ -364,7 +364,7 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
 
     # ---- the other page-queue variant
     others = {}
-    for v in ("page_array", "page_vlist"):
+    for v in ("page_array", "page_vlist", "chunk_array", "chunk_vlist"):
         if v == args.variant:
             continue
         with P.Heap(HEAP_BYTES, CHUNK, v) as h2:
