@@ -53,6 +53,9 @@ def parse():
                     help="heap size (smaller only for profiler captures)")
     ap.add_argument("--no-extras", action="store_true", help="headline only (used under a profiler)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--workload", choices=("sweep", "batching"), default="sweep",
+                    help="sweep: the headline size sweep; batching: 256 uneven batches, every form + autotuner")
+    ap.add_argument("--batches", type=int, default=256)
     return ap.parse_args()
 
 
@@ -202,10 +205,52 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def run_batching(args):
+    """256 request batches, threads per batch log-uniform in [2^10, 2^20], sizes
+    uniform in [4, 8192] B, 16 GiB heap: per-launch (4 and 1 launches per
+    batch), CUDA graph and persistent forms, then the autotuner."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2504_18211_gb300 as P
+    from paper_2504_18211_gb300 import batching as BT
+    from paper_2504_18211_gb300 import build as B
+    from paper_2504_18211_gb300 import workloads as W
+    B.build()
+    P.load()
+    sizes, offs = W.batching_workload(n_batches=args.batches)
+    run = BT.BatchRun(sizes, offs)
+    heap_bytes = 16 << 30
+    res = {"workload": f"batching: {args.batches} batches, {sizes.size} requests, sizes U[4,8192] B, 16 GiB heap",
+           "forms": {}}
+    with P.Heap(heap_bytes, 8192, args.variant) as heap:
+        for form in BT.FORMS:
+            ms = run.time(heap, form, reps=2)
+            res["forms"][form] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
+        got = run.checks()
+        st = heap.stats()
+        run.close()
+    o = offs.astype(np.int64)
+    want = [oracle.expected_checksums(sizes[o[b]:o[b + 1]], run.seed + b, 1) for b in range(offs.size - 1)]
+    res["verified"] = all(g == dict(w, nulls=0, mismatches=0) for g, w in zip(got, want)) and st["error_bits"] == 0
+    sub_sizes, sub_offs = sizes[: int(offs[16])], offs[:17]
+    tune_run = BT.BatchRun(sub_sizes, sub_offs)
+    best, table = BT.autotune(P.Heap, tune_run, heap_bytes)
+    res["autotune"] = {"best": best, "table": table, "trial": "first 16 batches, persistent form"}
+    if best:
+        with P.Heap(heap_bytes, best["chunk"], best["variant"]) as heap:
+            ms = run.time(heap, "persistent", reps=2, blocks_per_sm=best["warps_per_sm"] // 8)
+            res["tuned_persistent"] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batching":
+        return run_batching(args)
     import numpy as np
     import torch
 

@@ -223,6 +223,37 @@ ouro_status ouro_round_fused(ouro_heap *h, const uint32_t *d_sizes, size_t n, ui
  *     device error word is non-zero. */
 ouro_status ouro_heap_stats_static(ouro_heap *h, ouro_stats *out, void *stream);
 
+/* ---- batching: many request batches per pass ----------------------------- */
+
+/* One kernel for n_batches batches (Sec. 3 driver round per request):
+ * request i of batch b (d_sizes[d_offs[b] + i]) allocates, writes its
+ * pattern (seed + b, thread id i), reads it back and frees.  Warps pull
+ * 256-request tasks from *d_work (device scratch, 1 word, reset here);
+ * d_task_offs[b] = sum over batches before b of ceil(count/256), n_tasks
+ * its total.  d_out: n_batches checks (overwritten).  blocks_per_sm <= 0:
+ * the occupancy limit.  d_offs, d_task_offs: device arrays of n_batches+1. */
+ouro_status ouro_batches_persistent(ouro_heap *h, const uint32_t *d_sizes, const unsigned long long *d_offs,
+                                    const unsigned long long *d_task_offs, uint32_t n_batches, uint64_t n_tasks,
+                                    uint32_t seed, int mode, ouro_check *d_out, unsigned long long *d_work,
+                                    int blocks_per_sm, void *stream);
+
+/* Blocks of 256 threads per SM the persistent batching kernel of this
+ * heap's variant can keep resident (register limit); 0 on error. */
+int ouro_batches_max_blocks_per_sm(const ouro_heap *h);
+
+/* The same pass as one CUDA graph of per-batch launches, captured once.
+ * form 0: ouro_round_fused per batch; form 1: ouro_batch_malloc,
+ * ouro_pattern_write, ouro_pattern_check, ouro_batch_free per batch (d_ptrs:
+ * device scratch for the largest batch).  h_offs: HOST offsets (n_batches+1).
+ * Replay with ouro_batch_graph_launch; the captured pointers must stay valid. */
+typedef struct ouro_batch_graph ouro_batch_graph;
+ouro_status ouro_batch_graph_create(ouro_heap *h, const uint32_t *d_sizes, const unsigned long long *h_offs,
+                                    uint32_t n_batches, uint32_t seed, int mode, ouro_check *d_out,
+                                    void **d_ptrs, int form, ouro_batch_graph **out);
+ouro_status ouro_batch_graph_launch(ouro_batch_graph *g, void *stream);
+uint64_t ouro_batch_graph_nodes(const ouro_batch_graph *g);
+ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
+
 /* ---- measurement ------------------------------------------------------------ */
 
 /* L2 atomic throughput probe: `blocks` x 256 threads each do `iters` atomics on

@@ -102,6 +102,12 @@ def load(path: str = LIB_PATH):
         "ouro_probe_atomics": (st, [vp, sz, i32, u32, i32, vp]),
         "ouro_malloc_latency": (st, [vp, vp, vp, sz, vp, vp]),
         "ouro_heap_stats_static": (st, [vp, C.POINTER(Stats), vp]),
+        "ouro_batches_persistent": (st, [vp, vp, vp, vp, u32, u64, u32, i32, vp, vp, i32, vp]),
+        "ouro_batch_graph_create": (st, [vp, vp, vp, u32, u32, i32, vp, vp, i32, C.POINTER(vp)]),
+        "ouro_batch_graph_launch": (st, [vp, vp]),
+        "ouro_batch_graph_nodes": (u64, [vp]),
+        "ouro_batch_graph_destroy": (st, [vp]),
+        "ouro_batches_max_blocks_per_sm": (i32, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -267,3 +273,33 @@ def latency_bin_bounds(b: int):
         return b, b + 1
     l, q = b >> 2, b & 3
     return (1 << l) + q * (1 << (l - 2)), (1 << l) + (q + 1) * (1 << (l - 2))
+
+
+def ouro_batches_persistent(h: int, sizes, offs, task_offs, n_tasks: int, seed: int, mode: int, out, work,
+                            blocks_per_sm: int = 0, stream=None) -> None:
+    _check("ouro_batches_persistent", load().ouro_batches_persistent(
+        C.c_void_p(h), _ptr(sizes), _ptr(offs), _ptr(task_offs), offs.numel() - 1, n_tasks, seed & 0xFFFFFFFF,
+        mode, _ptr(out), _ptr(work), blocks_per_sm, _stream(stream)))
+
+
+def ouro_batch_graph_create(h: int, sizes, h_offs, seed: int, mode: int, out, ptrs=None, form: int = 0) -> int:
+    import numpy as np
+    offs = np.ascontiguousarray(h_offs, dtype=np.uint64)
+    g = C.c_void_p()
+    _check("ouro_batch_graph_create", load().ouro_batch_graph_create(
+        C.c_void_p(h), _ptr(sizes), offs.ctypes.data_as(C.c_void_p), offs.size - 1, seed & 0xFFFFFFFF, mode,
+        _ptr(out), _ptr(ptrs), form, C.byref(g)))
+    return g.value
+
+
+def ouro_batch_graph_launch(g: int, stream=None) -> None:
+    _check("ouro_batch_graph_launch", load().ouro_batch_graph_launch(C.c_void_p(g), _stream(stream)))
+
+
+def ouro_batch_graph_destroy(g: int) -> None:
+    _check("ouro_batch_graph_destroy", load().ouro_batch_graph_destroy(C.c_void_p(g)))
+
+
+def persistent_blocks_per_sm(heap) -> int:
+    """ouro_batches_max_blocks_per_sm for a Heap (or raw handle)."""
+    return int(load().ouro_batches_max_blocks_per_sm(C.c_void_p(getattr(heap, "h", heap))))

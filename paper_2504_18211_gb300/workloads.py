@@ -33,3 +33,15 @@ def uniform_sizes(threads: int, lo: int = 4, hi: int = 8192, seed: int = SEED_BA
 
 def single_size(threads: int, size: int) -> np.ndarray:
     return np.full(threads, size, dtype=np.uint32)
+
+
+def batching_workload(n_batches: int = 256, lo: float = 10.0, hi: float = 20.0, smin: int = 4, smax: int = 8192,
+                      seed: int = SEED_BASE + 3):
+    """Request batches: threads per batch round(2^u), u uniform in [lo, hi];
+    sizes uniform over the integers [smin, smax].  Returns (sizes, offs)
+    with batch b = sizes[offs[b]:offs[b+1]]."""
+    r = rng(seed)
+    threads = np.round(2.0 ** r.uniform(lo, hi, n_batches)).astype(np.int64)
+    sizes = r.integers(smin, smax + 1, size=int(threads.sum())).astype(np.uint32)
+    offs = np.concatenate([[0], np.cumsum(threads)]).astype(np.uint64)
+    return sizes, offs
