@@ -53,8 +53,9 @@ def parse():
                     help="heap size (smaller only for profiler captures)")
     ap.add_argument("--no-extras", action="store_true", help="headline only (used under a profiler)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", choices=("sweep", "batching"), default="sweep",
-                    help="sweep: the headline size sweep; batching: 256 uneven batches, every form + autotuner")
+    ap.add_argument("--workload", choices=("sweep", "batching", "serving"), default="sweep",
+                    help="sweep: the headline size sweep; batching: 256 uneven batches, every form + autotuner; "
+                         "serving: the device request loop")
     ap.add_argument("--batches", type=int, default=256)
     return ap.parse_args()
 
@@ -245,12 +246,61 @@ def run_batching(args):
     print(json.dumps(res))
 
 
+def run_serving(args):
+    """64 GiB heap of 16 KiB blocks; Poisson session arrivals (2000/s, 10 ms
+    steps); lognormal session sizes (median 4 MiB, sigma 1); one block per
+    session per step; admission up to 95 % of the blocks; 2000 steps in one
+    cooperative kernel."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2504_18211_gb300 as P
+    from paper_2504_18211_gb300 import build as B
+    from paper_2504_18211_gb300 import workloads as W
+    from paper_2504_18211_gb300.serving import ServeRun, model_schedule
+    B.build()
+    P.load()
+    steps, block, heap_bytes = 2000, 16384, 64 << 30
+    arrive, blocks = W.serving_workload(steps=steps)
+    cap = int(0.95 * heap_bytes // block)
+    res = {"workload": f"serving: {arrive.size} sessions arriving over {steps} steps of 10 ms (2000/s), "
+                       f"lognormal sizes median 4 MiB sigma 1 (<= 64 MiB), 16 KiB blocks, 64 GiB heap, cap 95 %"}
+    for variant in (args.variant, "chunk_array"):
+        run = ServeRun(arrive, blocks, n_slots=16384, max_blocks=4096, steps=steps)
+        with P.Heap(heap_bytes, block, variant) as heap:
+            ms = run.run(heap, cap)
+            r = run.results()
+            st = heap.stats()
+        admit, done, _ = model_schedule(arrive, blocks, steps, 16384, cap)
+        fin = np.flatnonzero(done >= 0)
+        sample = fin[:: max(1, fin.size // 64)]
+        ok = all((int(r["xor"][s]), int(r["sum"][s])) == (
+            lambda e: (e["xor64"], e["sum64"]))(oracle.expected_checksums(
+                np.full(int(blocks[s]), block, np.uint32), (run.seed + int(s)) & 0xFFFFFFFF, 1)) for s in sample)
+        lat = r["step_us"]
+        ops = r["mallocs"] + r["frees"]
+        res[variant] = {"ms": round(ms, 2), "mops": round(ops / (ms / 1e3) / 1e6, 1),
+                        "step_us_p50": round(float(np.percentile(lat, 50)), 1),
+                        "step_us_p99": round(float(np.percentile(lat, 99)), 1),
+                        "mallocs": r["mallocs"], "frees": r["frees"], "failed": r["failed"],
+                        "admitted": int((r["admit"] >= 0).sum()), "completed": int((r["done"] >= 0).sum()),
+                        "peak_committed_blocks_cap": cap,
+                        "verified": bool(ok and np.array_equal(r["admit"], admit) and np.array_equal(r["done"], done)
+                                         and r["error"] == 0 and st["error_bits"] == 0 and np.all(r["mism"][fin] == 0))}
+        del run
+        torch.cuda.empty_cache()
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batching":
         return run_batching(args)
+    if args.workload == "serving":
+        return run_serving(args)
     import numpy as np
     import torch
 

@@ -254,6 +254,29 @@ ouro_status ouro_batch_graph_launch(ouro_batch_graph *g, void *stream);
 uint64_t ouro_batch_graph_nodes(const ouro_batch_graph *g);
 ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
 
+/* ---- serving: a request loop on the device -------------------------------- */
+
+/* Run `steps` serving steps in ONE cooperative kernel.  Sessions (arrival
+ * order) arrive at step d_arrive_step[s] and grow by one block of
+ * block_bytes per step up to d_blocks[s] blocks (<= max_blocks), then free
+ * every block.  Admission, in arrival order: while a slot is free and the
+ * committed blocks of admitted sessions plus the newcomer's total stay <=
+ * cap_blocks.  Each block gets the driver-round pattern (seed + s, block
+ * index) and is read back; the session checksum folds every word.
+ * Device buffers (caller-owned; contents overwritten):
+ *   d_slot_session n_slots ints, d_slot_k n_slots, d_slot_acc 3*n_slots,
+ *   d_tables n_slots*max_blocks pointers, d_sess_out 5*n_sessions words
+ *   (xor, sum, mismatches, admit step, done step; all ones if never),
+ *   d_step_ns `steps` %globaltimer stamps, d_ctl 8 words (barrier state, next
+ *   arrival, committed blocks, error flag, mallocs, frees, failed mallocs).
+ * ENOTSUP if the device cannot launch cooperative kernels.  A grid barrier
+ * whose wait runs out sets d_ctl[4] and ends the kernel. */
+ouro_status ouro_serve(ouro_heap *h, const uint32_t *d_arrive_step, const uint32_t *d_blocks, uint32_t n_sessions,
+                       uint32_t n_slots, uint32_t max_blocks, int *d_slot_session, uint32_t *d_slot_k,
+                       unsigned long long *d_slot_acc, unsigned long long *d_tables, unsigned long long *d_sess_out,
+                       unsigned long long *d_step_ns, unsigned long long *d_ctl, uint32_t steps, uint32_t seed,
+                       uint64_t cap_blocks, uint32_t block_bytes, int blocks_per_sm, void *stream);
+
 /* ---- measurement ------------------------------------------------------------ */
 
 /* L2 atomic throughput probe: `blocks` x 256 threads each do `iters` atomics on

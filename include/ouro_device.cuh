@@ -43,7 +43,7 @@
 #define OURO_BUSY 0xFFFFFFFEu   /* successor segment being created by one thread */
 #define OURO_CLS_NONE 0xFFu
 #define OURO_CLS_SEG 0xFEu
-#define OURO_VL_HINTS 64
+#define OURO_VL_HINTS 1024
 #define OURO_NSTAT 8
 #define OURO_SHARDS 32
 #define OURO_SEG_HDR 64
@@ -317,6 +317,24 @@ __device__ inline void vl_event(const ouro_heap_dev &h, int c, const unsigned lo
   }
 }
 
+/* Position events of the lanes of mask (every lane of mask calls): lanes
+ * with `active` and a slot count one event on the segment of their slot;
+ * lanes on the same segment are summed into one atomic. */
+__device__ inline void vl_event_warp(const ouro_heap_dev &h, int c, const unsigned long long *cell, bool active,
+                                     unsigned mask) {
+  const bool on = active && cell;
+  const unsigned x = on ? (unsigned)(((const unsigned char *)cell - h.base) >> h.log2_chunk) : OURO_NIL;
+  const unsigned g = __match_any_sync(mask, x) & __ballot_sync(mask, on);
+  if (on && laneid() == (unsigned)(__ffs(g) - 1)) {
+    const unsigned n = __popc(g);
+    const unsigned r = atomicAdd(&seg_of(h, x)->done, n) + n;
+    if (r == 2u * h.seg_cap) {
+      __threadfence();
+      vl_advance(h, c);
+    }
+  }
+}
+
 /* Slot of position pos in the virtualized list of class c.  create: link
  * missing segments (producers); otherwise null while the segment is not
  * linked yet.  One thread creates each segment: it first claims the empty
@@ -544,15 +562,20 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
     __threadfence();
     __syncwarp(vmask);
     const unsigned long long total = (unsigned long long)m << ppc_log;
-    for (unsigned long long i = rk; i < total; i += nl) {
-      unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
-      unsigned item = (x << ppc_log) | (unsigned)(i & (ppc - 1));
-      unsigned long long p = t0 + i;
-      unsigned long long *cell = slot_at<VL>(h, c, p, true);
-      if (!cell) continue;   /* queue storage exhausted: recorded */
-      int rc = put_at(h, cell, p, item, false);
-      if (VL) vl_event(h, c, cell, 1);
-      if (rc == 1) push_one<VL>(h, c, item);
+    for (unsigned long long i0 = 0; i0 < total; i0 += nl) {
+      const unsigned long long i = i0 + rk;
+      const bool act = i < total;
+      unsigned long long *cell = nullptr;
+      int rc = 0;
+      unsigned item = 0;
+      if (act) {
+        const unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
+        item = (x << ppc_log) | (unsigned)(i & (ppc - 1));
+        cell = slot_at<VL>(h, c, t0 + i, true);
+        if (cell) rc = put_at(h, cell, t0 + i, item, false);   /* no slot: queue storage exhausted (recorded) */
+      }
+      if (VL) vl_event_warp(h, c, cell, act, vmask);
+      if (act && rc == 1) push_one<VL>(h, c, item);
     }
   }
   if (exhausted) {
@@ -567,12 +590,12 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
     }
     dt = __shfl_sync(vmask, dt, owner);
     dn = __shfl_sync(vmask, dn, owner);
-    for (unsigned long long i = rk; i < dn; i += nl) {
-      unsigned long long p = dt + i;
-      unsigned long long *cell = slot_at<VL>(h, c, p, true);
-      if (!cell) continue;
-      put_at(h, cell, p, 0, true);
-      if (VL) vl_event(h, c, cell, 1);
+    for (unsigned long long i0 = 0; i0 < dn; i0 += nl) {
+      const unsigned long long i = i0 + rk;
+      const bool act = i < dn;
+      unsigned long long *cell = act ? slot_at<VL>(h, c, dt + i, true) : nullptr;
+      if (cell) put_at(h, cell, dt + i, 0, true);
+      if (VL) vl_event_warp(h, c, cell, act, vmask);
     }
   }
   __syncwarp(vmask);
@@ -591,13 +614,23 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long pos = 0;
   if (lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
-  pos = __shfl_sync(vmask, pos, leader) + rank;
+  const unsigned long long p0 = __shfl_sync(vmask, pos, leader);
+  pos = p0 + rank;
 
   unsigned item = 0;
   int st = 0;   /* 0 waiting, 1 item, 2 null answer, 3 gave up */
-  unsigned long long *cell = slot_at<VL>(h, cls, pos, false);
+  unsigned long long *cell;
+  if (VL) {   /* the leader finds its segment; lanes in the same segment reuse it */
+    unsigned long long *c0 = lane == leader ? vl_slot(h, cls, p0, false) : nullptr;
+    c0 = reinterpret_cast<unsigned long long *>(
+        __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
+    cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + rank : vl_slot(h, cls, pos, false);
+  } else {
+    cell = ring_slot(h, cls, pos);
+  }
   if (cell) st = try_take<VL>(h, cls, cell, pos, &item);
 
+  bool gave_up = false;
   if (__ballot_sync(vmask, st == 0)) {
     unsigned ns = h.backoff_min_ns;
     for (unsigned it = 0;; ++it) {
@@ -627,6 +660,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
           if (!cell) cell = slot_at<VL>(h, cls, pos, true);
           int g = cell ? give_up<VL>(h, cls, cell, pos, &item) : 0;
           st = g ? g : 3;
+          gave_up = g == 3;
           if (st == 3) {
             set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_PAGE_GIVEUP);
             stat_add(h, cls, OURO_ST_CANCEL, 1);
@@ -642,7 +676,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       }
     }
   }
-  if (VL && cell && st != 0) vl_event(h, cls, cell, 1);
+  if (VL) vl_event_warp(h, cls, cell, st != 0 && (st != 3 || gave_up), vmask);
 
   void *res = nullptr;
   if (st == 1) {
@@ -678,11 +712,19 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
     t = atomicAdd(&q->tail.v, (unsigned long long)__popc(grp));
     stat_add(h, cls, OURO_ST_FREE, __popc(grp));
   }
-  t = __shfl_sync(vmask, t, leader) + rank;
-  unsigned long long *cell = slot_at<VL>(h, cls, t, true);
-  if (!cell) return;   /* queue storage exhausted (recorded): the page is lost */
-  int rc = put_at(h, cell, t, item, false);
-  if (VL) vl_event(h, cls, cell, 1);
+  const unsigned long long t0 = __shfl_sync(vmask, t, leader);
+  t = t0 + rank;
+  unsigned long long *cell;
+  if (VL) {   /* the leader finds (or links) its segment; lanes in the same segment reuse it */
+    unsigned long long *c0 = lane == leader ? vl_slot(h, cls, t0, true) : nullptr;
+    c0 = reinterpret_cast<unsigned long long *>(
+        __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
+    cell = (c0 && t / h.seg_cap == t0 / h.seg_cap) ? c0 + rank : vl_slot(h, cls, t, true);
+  } else {
+    cell = ring_slot(h, cls, t);
+  }
+  int rc = cell ? put_at(h, cell, t, item, false) : 0;   /* no slot: queue storage exhausted, page lost (recorded) */
+  if (VL) vl_event_warp(h, cls, cell, true, vmask);
   if (rc == 1) {
     stat_add(h, cls, OURO_ST_REPUSH, 1);
     push_one<VL>(h, cls, item);
@@ -832,7 +874,7 @@ __device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int o
       if (i >= D || !cell[r]) continue;
       const bool isnull = item[r] == 0xffffffffu;
       int rc = put_at(h, cell[r], t + i, isnull ? 0 : item[r], isnull);
-      if (VL) vl_event(h, c, cell[r], 1);
+      if (VL) vl_event(h, c, cell[r], 1);   /* planned positions: at most 8 per lane */
       if (rc == 1 && !isnull) {   /* its group gave up: hand the reserved pages back */
         const unsigned x = OURO_CQ_ID(item[r]);
         int before = atomicAdd(&h.chunk_free[x], (int)OURO_CQ_CNT(item[r]));

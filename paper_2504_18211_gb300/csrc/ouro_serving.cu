@@ -1,0 +1,252 @@
+/*
+ * Serving: a request loop that stays on the device (one cooperative,
+ * persistent kernel for all steps) over sessions whose memory grows.
+ *
+ * Each step:
+ *   1. admission (block 0, thread 0): sessions that have arrived are admitted
+ *      in arrival order while a session slot is free and the blocks committed
+ *      to admitted sessions, plus the newcomer's total, stay within the
+ *      admission cap (95 % of the heap's blocks);
+ *   2. growth (all warps): every active session allocates one block with
+ *      ouro_malloc, records it in its block table, writes its pattern
+ *      (seed + session id, block index) and reads it back through L2,
+ *      folding the words into the session checksum;
+ *   3. completion (all warps): a session that reached its size frees every
+ *      block and reports its checksum; its slot is free for the next step.
+ * The allocator state, the session table and the block tables stay resident
+ * for the whole run; requests that arrive while others are running are
+ * admitted as slots and memory free up, and their work overlaps on the GPU.
+ * Step boundaries are a grid barrier of this file (every wait bounded); one
+ * thread stamps %globaltimer after each step for the latency histogram.
+ */
+#include "ouro_internal.cuh"
+#include "ouro_payload.cuh"
+
+using namespace ouro::detail;
+
+namespace {
+
+struct serve_args {
+  ouro_heap_dev h;
+  /* sessions, in arrival order */
+  const uint32_t *arrive_step;   /* step at which the session has arrived */
+  const uint32_t *blocks;        /* total blocks the session grows to */
+  uint32_t n_sessions;
+  /* slots */
+  uint32_t n_slots, max_blocks;
+  int *slot_session;             /* session id or -1 */
+  uint32_t *slot_k;              /* blocks allocated so far */
+  unsigned long long *slot_acc;  /* per slot: xor, sum, mismatches */
+  unsigned long long *tables;    /* n_slots x max_blocks block pointers */
+  /* results */
+  unsigned long long *sess_out;  /* per session: xor, sum, mismatches, admit step, done step (u64 each) */
+  unsigned long long *step_ns;   /* per step: %globaltimer at its end */
+  unsigned long long *ctl;       /* [0] barrier count, [1] barrier generation, [2] next arrival,
+                                    [3] committed blocks, [4] error, [5] mallocs, [6] frees, [7] failed */
+  uint32_t steps;
+  uint32_t seed;
+  unsigned long long cap_blocks; /* admission cap */
+  uint32_t block_bytes;
+  uint32_t spin_limit;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+/* grid barrier for a cooperative launch; a wait that runs out sets ctl[4] */
+__device__ bool grid_barrier(unsigned long long *ctl, unsigned nblocks, unsigned limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned long long gen = ld_acq(&ctl[1]);
+    __threadfence();
+    if (atomicAdd(&ctl[0], 1ull) == nblocks - 1) {
+      st_rlx(&ctl[0], 0ull);
+      __threadfence();
+      atomicAdd(&ctl[1], 1ull);
+    } else {
+      unsigned it = 0;
+      while (ld_acq(&ctl[1]) == gen) {
+        if (++it > limit) {
+          atomicExch(&ctl[4], 1ull);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    if (ld_acq(&ctl[4])) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+/* Pattern of one block, written and read back by the whole warp; the
+ * block's folded checksum lands in (x, s, mism) of every lane. */
+__device__ void serve_block_payload(unsigned char *bp, uint32_t bytes, uint32_t key, unsigned long long &x,
+                                    unsigned long long &s, unsigned long long &mism) {
+  const unsigned lane = laneid();
+  uint4 *u4 = reinterpret_cast<uint4 *>(bp);
+  const uint32_t units = bytes >> 4;
+#pragma unroll 4
+  for (uint32_t u = lane; u < units; u += 32) u4[u] = pat4(key, 4 * u);
+  __syncwarp();
+  payload_acc a;
+  for (uint32_t u = (lane + 1) & 31; u < units; u += 32) check4(__ldcg(u4 + u), pat4(key, 4 * u), a);
+  for (int o = 16; o; o >>= 1) {
+    a.x ^= __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.s += __shfl_xor_sync(0xffffffffu, a.s, o);
+    a.mism += __shfl_xor_sync(0xffffffffu, a.mism, o);
+  }
+  x = a.x;
+  s = a.s;
+  mism = a.mism;
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_serve(serve_args A) {
+  const unsigned lane = laneid();
+  const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+  const ouro_heap_dev &h = A.h;
+  for (uint32_t step = 0; step < A.steps; ++step) {
+    /* 1. admission */
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      unsigned long long next = A.ctl[2], committed = A.ctl[3];
+      uint32_t free_slot = 0;
+      while (next < A.n_sessions && A.arrive_step[next] <= step &&
+             committed + A.blocks[next] <= A.cap_blocks) {
+        while (free_slot < A.n_slots && A.slot_session[free_slot] >= 0) ++free_slot;
+        if (free_slot == A.n_slots) break;
+        A.slot_session[free_slot] = (int)next;
+        A.slot_k[free_slot] = 0;
+        A.slot_acc[3 * free_slot] = A.slot_acc[3 * free_slot + 1] = A.slot_acc[3 * free_slot + 2] = 0;
+        A.sess_out[5 * next + 3] = step;
+        committed += A.blocks[next];
+        ++next;
+      }
+      A.ctl[2] = next;
+      A.ctl[3] = committed;
+      __threadfence();
+    }
+    if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
+    /* 2. growth: one session per lane, warps over the slots */
+    for (uint32_t s0 = warp * 32; s0 < A.n_slots; s0 += nwarps * 32) {
+      const uint32_t slot = s0 + lane;
+      const int sess = slot < A.n_slots ? A.slot_session[slot] : -1;
+      const uint32_t k = sess >= 0 ? A.slot_k[slot] : 0;
+      const bool grow = sess >= 0 && k < A.blocks[sess];
+      unsigned char *p = nullptr;
+      if (grow) {
+        p = static_cast<unsigned char *>(malloc_v<V>(h, A.block_bytes));
+        if (p) {
+          A.tables[(size_t)slot * A.max_blocks + k] = reinterpret_cast<unsigned long long>(p);
+          A.slot_k[slot] = k + 1;
+        }
+      }
+      __syncwarp();
+      const unsigned okm = __ballot_sync(0xffffffffu, p != nullptr);
+      const unsigned growm = __ballot_sync(0xffffffffu, grow);
+      if (lane == 0 && growm) {
+        atomicAdd(&A.ctl[5], (unsigned long long)__popc(okm));
+        if (growm != okm) atomicAdd(&A.ctl[7], (unsigned long long)(__popc(growm) - __popc(okm)));
+      }
+      for (unsigned j = 0; j < 32; ++j) {
+        if (!((okm >> j) & 1)) continue;
+        const unsigned long long bp = __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(p), j);
+        const uint32_t key_sess = __shfl_sync(0xffffffffu, (uint32_t)sess, j);
+        const uint32_t key_k = __shfl_sync(0xffffffffu, k, j);
+        const uint32_t key = fmix32((A.seed + key_sess) ^ (key_k * OURO_GOLD));
+        unsigned long long x, sum, mism;
+        serve_block_payload(reinterpret_cast<unsigned char *>(bp), A.block_bytes, key, x, sum, mism);
+        if (lane == j) {
+          A.slot_acc[3 * slot] ^= x;
+          A.slot_acc[3 * slot + 1] += sum;
+          A.slot_acc[3 * slot + 2] += mism;
+        }
+      }
+    }
+    if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
+    /* 3. completion: a warp per finished session frees its blocks */
+    for (uint32_t slot = warp; slot < A.n_slots; slot += nwarps) {
+      const int sess = A.slot_session[slot];
+      if (sess < 0 || A.slot_k[slot] < A.blocks[sess]) continue;
+      const uint32_t nb = A.slot_k[slot];
+      for (uint32_t b0 = 0; b0 < nb; b0 += 32) {
+        const uint32_t b = b0 + lane;
+        void *p = b < nb ? reinterpret_cast<void *>(A.tables[(size_t)slot * A.max_blocks + b]) : nullptr;
+        if (b < nb) free_v<V>(h, p);
+        __syncwarp();
+      }
+      if (lane == 0) {
+        atomicAdd(&A.ctl[6], (unsigned long long)nb);
+        A.sess_out[5 * sess + 0] = A.slot_acc[3 * slot];
+        A.sess_out[5 * sess + 1] = A.slot_acc[3 * slot + 1];
+        A.sess_out[5 * sess + 2] = A.slot_acc[3 * slot + 2];
+        A.sess_out[5 * sess + 4] = step;
+        atomicAdd(&A.ctl[3], 0ull - (unsigned long long)A.blocks[sess]);
+        A.slot_session[slot] = -1;
+      }
+      __syncwarp();
+    }
+    if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[step] = globaltimer();
+  }
+}
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, const uint32_t *d_blocks,
+                                  uint32_t n_sessions, uint32_t n_slots, uint32_t max_blocks, int *d_slot_session,
+                                  uint32_t *d_slot_k, unsigned long long *d_slot_acc, unsigned long long *d_tables,
+                                  unsigned long long *d_sess_out, unsigned long long *d_step_ns,
+                                  unsigned long long *d_ctl, uint32_t steps, uint32_t seed, uint64_t cap_blocks,
+                                  uint32_t block_bytes, int blocks_per_sm, void *stream) {
+  if (!H || !d_arrive_step || !d_blocks || !d_slot_session || !d_slot_k || !d_slot_acc || !d_tables ||
+      !d_sess_out || !d_step_ns || !d_ctl || n_slots == 0 || max_blocks == 0 || (block_bytes & 15) ||
+      block_bytes == 0 || block_bytes > H->d.chunk_bytes)
+    return OURO_EINVAL;
+  cudaStream_t s = S(stream);
+  OURO_CUDA(cudaMemsetAsync(d_slot_session, 0xFF, n_slots * sizeof(int), s));
+  OURO_CUDA(cudaMemsetAsync(d_ctl, 0, 8 * 8, s));
+  OURO_CUDA(cudaMemsetAsync(d_sess_out, 0xFF, (size_t)n_sessions * 5 * 8, s));
+  serve_args A;
+  A.h = H->d;
+  A.arrive_step = d_arrive_step;
+  A.blocks = d_blocks;
+  A.n_sessions = n_sessions;
+  A.n_slots = n_slots;
+  A.max_blocks = max_blocks;
+  A.slot_session = d_slot_session;
+  A.slot_k = d_slot_k;
+  A.slot_acc = d_slot_acc;
+  A.tables = d_tables;
+  A.sess_out = d_sess_out;
+  A.step_ns = d_step_ns;
+  A.ctl = d_ctl;
+  A.steps = steps;
+  A.seed = seed;
+  A.cap_blocks = cap_blocks;
+  A.block_bytes = block_bytes;
+  A.spin_limit = 1u << 24;   /* barrier wait: ~2 s of 128 ns naps, far above any step */
+  int dev = 0, coop = 0, per_sm = 0;
+  OURO_CUDA(cudaGetDevice(&dev));
+  OURO_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return OURO_ENOTSUP;
+  void *args[] = {&A};
+  OURO_DISPATCH(H->d.variant, ({
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<V>, 256, 0);
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    if (per_sm < 1) per_sm = 1;
+    OURO_CUDA(cudaLaunchCooperativeKernel((const void *)k_serve<V>, dim3(per_sm * ouro::host::sm_count()),
+                                          dim3(256), args, 0, s));
+  }));
+  OURO_LAUNCHED();
+  return OURO_OK;
+}

@@ -45,3 +45,20 @@ def batching_workload(n_batches: int = 256, lo: float = 10.0, hi: float = 20.0, 
     sizes = r.integers(smin, smax + 1, size=int(threads.sum())).astype(np.uint32)
     offs = np.concatenate([[0], np.cumsum(threads)]).astype(np.uint64)
     return sizes, offs
+
+
+def serving_workload(steps: int = 2000, rate: float = 2000.0, dt: float = 0.01, median_bytes: int = 4 << 20,
+                     sigma: float = 1.0, block_bytes: int = 16384, max_blocks: int = 4096,
+                     seed: int = SEED_BASE + 4):
+    """Sessions arriving as a Poisson process (rate per second) on a virtual
+    clock of `steps` steps of dt seconds; each session's total size is
+    lognormal (median, sigma), in blocks of block_bytes, at most max_blocks.
+    Returns (arrive_step, blocks), sessions in arrival order."""
+    r = rng(seed)
+    horizon = steps * dt
+    n = int(r.poisson(rate * horizon))
+    t = np.sort(r.uniform(0.0, horizon, n))
+    arrive = np.minimum(np.floor(t / dt), steps - 1).astype(np.uint32)
+    size = r.lognormal(np.log(median_bytes), sigma, n)
+    blocks = np.clip(np.ceil(size / block_bytes), 1, max_blocks).astype(np.uint32)
+    return arrive, blocks
