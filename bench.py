@@ -53,7 +53,7 @@ def parse():
                     help="heap size (smaller only for profiler captures)")
     ap.add_argument("--no-extras", action="store_true", help="headline only (used under a profiler)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", choices=("sweep", "batching", "serving"), default="sweep",
+    ap.add_argument("--workload", choices=("sweep", "batching", "serving", "graph"), default="sweep",
                     help="sweep: the headline size sweep; batching: 256 uneven batches, every form + autotuner; "
                          "serving: the device request loop")
     ap.add_argument("--batches", type=int, default=256)
@@ -293,6 +293,50 @@ def run_serving(args):
     print(json.dumps(res))
 
 
+def run_graph(args):
+    """2^20 vertices, 2^24 directed edges with power-law endpoints (degree
+    exponent 2.1), lists from 4 entries growing by malloc 2x / copy / free
+    old, 16 GiB heap of 8 KiB chunks; one insertion kernel timed."""
+    import numpy as np
+    import torch
+
+    import paper_2504_18211_gb300 as P
+    from paper_2504_18211_gb300 import build as B
+    from paper_2504_18211_gb300 import workloads as W
+    from paper_2504_18211_gb300.graph import GraphRun, expected_class_counts
+    B.build()
+    P.load()
+    nv, ne, chunk, heap_bytes = 1 << 20, 1 << 24, 8192, 16 << 30
+    src, dst = W.graph_workload(nv, ne)
+    res = {"workload": "graph growth: 2^20 vertices, 2^24 edges, power-law endpoints (alpha 2.1), "
+                       "lists 4 -> doubling -> one chunk -> chained 8 KiB segments, 16 GiB heap"}
+    for variant in (args.variant, "chunk_array"):
+        g = GraphRun(src, dst, nv)
+        with P.Heap(heap_bytes, chunk, variant) as heap:
+            g.init(heap)
+            torch.cuda.synchronize()
+            st0 = heap.stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.insert(heap)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            st = heap.stats()
+            deg = g.degrees()
+            m, f, _ = expected_class_counts(deg, chunk, heap.n_classes)
+            ops = sum(st["mallocs"]) + sum(st["frees"]) - sum(st0["mallocs"])
+            ok = (np.array_equal(deg, np.bincount(src, minlength=nv)) and st["mallocs"] == m.tolist()
+                  and st["frees"] == f.tolist() and st["error_bits"] == 0 and g.ctl_dict()["failed"] == 0)
+            res[variant] = {"ms": round(ms, 2), "appends_per_s": round(ne / (ms / 1e3), 1),
+                            "alloc_ops": ops, "alloc_mops": round(ops / (ms / 1e3) / 1e6, 2),
+                            "max_degree": int(deg.max()), "verified": bool(ok)}
+            g.free(heap)
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -301,6 +345,8 @@ def main():
         return run_batching(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "graph":
+        return run_graph(args)
     import numpy as np
     import torch
 

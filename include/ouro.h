@@ -267,15 +267,39 @@ ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
  *   d_slot_session n_slots ints, d_slot_k n_slots, d_slot_acc 3*n_slots,
  *   d_tables n_slots*max_blocks pointers, d_sess_out 5*n_sessions words
  *   (xor, sum, mismatches, admit step, done step; all ones if never),
- *   d_step_ns `steps` %globaltimer stamps, d_ctl 8 words (barrier state, next
- *   arrival, committed blocks, error flag, mallocs, frees, failed mallocs).
+ *   d_step_ns `steps` %globaltimer stamps, d_ctl 9 words (barrier state, next
+ *   arrival, committed blocks, error flag, mallocs, frees, failed mallocs,
+ *   free-slot stack top), d_free_stack n_slots slot ids.
  * ENOTSUP if the device cannot launch cooperative kernels.  A grid barrier
  * whose wait runs out sets d_ctl[4] and ends the kernel. */
 ouro_status ouro_serve(ouro_heap *h, const uint32_t *d_arrive_step, const uint32_t *d_blocks, uint32_t n_sessions,
                        uint32_t n_slots, uint32_t max_blocks, int *d_slot_session, uint32_t *d_slot_k,
                        unsigned long long *d_slot_acc, unsigned long long *d_tables, unsigned long long *d_sess_out,
-                       unsigned long long *d_step_ns, unsigned long long *d_ctl, uint32_t steps, uint32_t seed,
-                       uint64_t cap_blocks, uint32_t block_bytes, int blocks_per_sm, void *stream);
+                       unsigned long long *d_step_ns, unsigned long long *d_ctl, uint32_t *d_free_stack,
+                       uint32_t steps, uint32_t seed, uint64_t cap_blocks, uint32_t block_bytes, int blocks_per_sm,
+                       void *stream);
+
+/* ---- graph growth: adjacency lists grown in kernels --------------------------- */
+
+/* Bytes of one vertex record (d_vertices holds n_vertices of them, device). */
+size_t ouro_graph_vertex_bytes(void);
+/* Every vertex gets an empty list of 4 entries (16 B from the heap).
+ * d_ctl (device, 4 words, cleared): [0] entries appended, [1] failed
+ * mallocs, [2] entries skipped after a lock wait ran out. */
+ouro_status ouro_graph_init(ouro_heap *h, void *d_vertices, uint32_t n_vertices, unsigned long long *d_ctl,
+                            void *stream);
+/* Append edge e's d_dst[e] to vertex d_src[e]'s list for all n_edges: a
+ * list that is full doubles (malloc 2x, copy, free old) one step at a time
+ * up to one chunk of entries, then grows by chained one-chunk overflow
+ * segments.  Per-vertex locks, bounded. */
+ouro_status ouro_graph_insert(ouro_heap *h, void *d_vertices, const uint32_t *d_src, const uint32_t *d_dst,
+                              uint64_t n_edges, unsigned long long *d_ctl, void *stream);
+/* Copy every vertex's entries to d_out[d_offsets[v] ..] (offsets = prefix
+ * sum of the degrees) for checking. */
+ouro_status ouro_graph_gather(ouro_heap *h, const void *d_vertices, uint32_t n_vertices,
+                              const unsigned long long *d_offsets, uint32_t *d_out, void *stream);
+/* Free every list and overflow segment. */
+ouro_status ouro_graph_free(ouro_heap *h, void *d_vertices, uint32_t n_vertices, void *stream);
 
 /* ---- measurement ------------------------------------------------------------ */
 

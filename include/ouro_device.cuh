@@ -160,7 +160,7 @@ enum {
   OURO_SITE_SPARE = 1, OURO_SITE_VL_FIRST, OURO_SITE_VL_NEXT, OURO_SITE_VL_WALK, OURO_SITE_PUT,
   OURO_SITE_PUSH_ONE, OURO_SITE_PAGE_GIVEUP, OURO_SITE_PAGE_CHECKED, OURO_SITE_CLAIM,
   OURO_SITE_CHUNK_GIVEUP, OURO_SITE_CHUNK_DOUBLE, OURO_SITE_BAD_FREE, OURO_SITE_PAGE_DOUBLE,
-  OURO_SITE_TRIM
+  OURO_SITE_TRIM, OURO_SITE_GRAPH_LOCK
 };
 __device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits, unsigned site) {
   atomicOr(&gl(h)->error_bits, bits);

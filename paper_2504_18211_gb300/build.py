@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libouro.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ouro_host.cu", "ouro_kernels.cu", "ouro_probe.cu", "ouro_batching.cu", "ouro_serving.cu"]
+SOURCES = ["ouro_host.cu", "ouro_kernels.cu", "ouro_probe.cu", "ouro_batching.cu", "ouro_serving.cu", "ouro_graph.cu"]
 
 
 def nvcc() -> str:

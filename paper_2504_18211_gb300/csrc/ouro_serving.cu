@@ -42,7 +42,9 @@ struct serve_args {
   unsigned long long *sess_out;  /* per session: xor, sum, mismatches, admit step, done step (u64 each) */
   unsigned long long *step_ns;   /* per step: %globaltimer at its end */
   unsigned long long *ctl;       /* [0] barrier count, [1] barrier generation, [2] next arrival,
-                                    [3] committed blocks, [4] error, [5] mallocs, [6] frees, [7] failed */
+                                    [3] committed blocks, [4] error, [5] mallocs, [6] frees, [7] failed,
+                                    [8] free-slot stack top */
+  uint32_t *free_stack;          /* free slot ids (stack of n_slots) */
   uint32_t steps;
   uint32_t seed;
   unsigned long long cap_blocks; /* admission cap */
@@ -113,61 +115,57 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
   const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
   const ouro_heap_dev &h = A.h;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_slots; i += gridDim.x * blockDim.x)
+    A.free_stack[i] = A.n_slots - 1 - i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl[8] = A.n_slots;
+  if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
   for (uint32_t step = 0; step < A.steps; ++step) {
-    /* 1. admission */
+    /* 1. admission: arrival order, a free slot (stack), committed + newcomer <= cap */
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      unsigned long long next = A.ctl[2], committed = A.ctl[3];
-      uint32_t free_slot = 0;
-      while (next < A.n_sessions && A.arrive_step[next] <= step &&
-             committed + A.blocks[next] <= A.cap_blocks) {
-        while (free_slot < A.n_slots && A.slot_session[free_slot] >= 0) ++free_slot;
-        if (free_slot == A.n_slots) break;
-        A.slot_session[free_slot] = (int)next;
-        A.slot_k[free_slot] = 0;
-        A.slot_acc[3 * free_slot] = A.slot_acc[3 * free_slot + 1] = A.slot_acc[3 * free_slot + 2] = 0;
+      unsigned long long next = A.ctl[2], committed = A.ctl[3], top = A.ctl[8];
+      while (next < A.n_sessions && A.arrive_step[next] <= step && committed + A.blocks[next] <= A.cap_blocks &&
+             top > 0) {
+        const uint32_t slot = A.free_stack[--top];
+        A.slot_session[slot] = (int)next;
+        A.slot_k[slot] = 0;
+        A.slot_acc[3 * slot] = A.slot_acc[3 * slot + 1] = A.slot_acc[3 * slot + 2] = 0;
         A.sess_out[5 * next + 3] = step;
         committed += A.blocks[next];
         ++next;
       }
       A.ctl[2] = next;
       A.ctl[3] = committed;
+      A.ctl[8] = top;
       __threadfence();
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
-    /* 2. growth: one session per lane, warps over the slots */
-    for (uint32_t s0 = warp * 32; s0 < A.n_slots; s0 += nwarps * 32) {
-      const uint32_t slot = s0 + lane;
-      const int sess = slot < A.n_slots ? A.slot_session[slot] : -1;
-      const uint32_t k = sess >= 0 ? A.slot_k[slot] : 0;
-      const bool grow = sess >= 0 && k < A.blocks[sess];
-      unsigned char *p = nullptr;
-      if (grow) {
-        p = static_cast<unsigned char *>(malloc_v<V>(h, A.block_bytes));
-        if (p) {
-          A.tables[(size_t)slot * A.max_blocks + k] = reinterpret_cast<unsigned long long>(p);
+    /* 2. growth: one session per warp: lane 0 allocates, the warp writes and
+     *    reads back the block */
+    for (uint32_t slot = warp; slot < A.n_slots; slot += nwarps) {
+      const int sess = A.slot_session[slot];
+      if (sess < 0) continue;
+      const uint32_t k = A.slot_k[slot];
+      if (k >= A.blocks[sess]) continue;
+      unsigned long long bp = 0;
+      if (lane == 0) {
+        bp = reinterpret_cast<unsigned long long>(malloc_v<V>(h, A.block_bytes));
+        if (bp) {
+          A.tables[(size_t)slot * A.max_blocks + k] = bp;
           A.slot_k[slot] = k + 1;
+          atomicAdd(&A.ctl[5], 1ull);
+        } else {
+          atomicAdd(&A.ctl[7], 1ull);
         }
       }
-      __syncwarp();
-      const unsigned okm = __ballot_sync(0xffffffffu, p != nullptr);
-      const unsigned growm = __ballot_sync(0xffffffffu, grow);
-      if (lane == 0 && growm) {
-        atomicAdd(&A.ctl[5], (unsigned long long)__popc(okm));
-        if (growm != okm) atomicAdd(&A.ctl[7], (unsigned long long)(__popc(growm) - __popc(okm)));
-      }
-      for (unsigned j = 0; j < 32; ++j) {
-        if (!((okm >> j) & 1)) continue;
-        const unsigned long long bp = __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(p), j);
-        const uint32_t key_sess = __shfl_sync(0xffffffffu, (uint32_t)sess, j);
-        const uint32_t key_k = __shfl_sync(0xffffffffu, k, j);
-        const uint32_t key = fmix32((A.seed + key_sess) ^ (key_k * OURO_GOLD));
-        unsigned long long x, sum, mism;
-        serve_block_payload(reinterpret_cast<unsigned char *>(bp), A.block_bytes, key, x, sum, mism);
-        if (lane == j) {
-          A.slot_acc[3 * slot] ^= x;
-          A.slot_acc[3 * slot + 1] += sum;
-          A.slot_acc[3 * slot + 2] += mism;
-        }
+      bp = __shfl_sync(0xffffffffu, bp, 0);
+      if (!bp) continue;
+      const uint32_t key = fmix32((A.seed + (uint32_t)sess) ^ (k * OURO_GOLD));
+      unsigned long long x, sum, mism;
+      serve_block_payload(reinterpret_cast<unsigned char *>(bp), A.block_bytes, key, x, sum, mism);
+      if (lane == 0) {
+        A.slot_acc[3 * slot] ^= x;
+        A.slot_acc[3 * slot + 1] += sum;
+        A.slot_acc[3 * slot + 2] += mism;
       }
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
@@ -190,6 +188,7 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
         A.sess_out[5 * sess + 4] = step;
         atomicAdd(&A.ctl[3], 0ull - (unsigned long long)A.blocks[sess]);
         A.slot_session[slot] = -1;
+        A.free_stack[atomicAdd(&A.ctl[8], 1ull)] = slot;
       }
       __syncwarp();
     }
@@ -206,15 +205,15 @@ extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, c
                                   uint32_t n_sessions, uint32_t n_slots, uint32_t max_blocks, int *d_slot_session,
                                   uint32_t *d_slot_k, unsigned long long *d_slot_acc, unsigned long long *d_tables,
                                   unsigned long long *d_sess_out, unsigned long long *d_step_ns,
-                                  unsigned long long *d_ctl, uint32_t steps, uint32_t seed, uint64_t cap_blocks,
-                                  uint32_t block_bytes, int blocks_per_sm, void *stream) {
+                                  unsigned long long *d_ctl, uint32_t *d_free_stack, uint32_t steps, uint32_t seed,
+                                  uint64_t cap_blocks, uint32_t block_bytes, int blocks_per_sm, void *stream) {
   if (!H || !d_arrive_step || !d_blocks || !d_slot_session || !d_slot_k || !d_slot_acc || !d_tables ||
-      !d_sess_out || !d_step_ns || !d_ctl || n_slots == 0 || max_blocks == 0 || (block_bytes & 15) ||
+      !d_sess_out || !d_step_ns || !d_ctl || !d_free_stack || n_slots == 0 || max_blocks == 0 || (block_bytes & 15) ||
       block_bytes == 0 || block_bytes > H->d.chunk_bytes)
     return OURO_EINVAL;
   cudaStream_t s = S(stream);
   OURO_CUDA(cudaMemsetAsync(d_slot_session, 0xFF, n_slots * sizeof(int), s));
-  OURO_CUDA(cudaMemsetAsync(d_ctl, 0, 8 * 8, s));
+  OURO_CUDA(cudaMemsetAsync(d_ctl, 0, 9 * 8, s));
   OURO_CUDA(cudaMemsetAsync(d_sess_out, 0xFF, (size_t)n_sessions * 5 * 8, s));
   serve_args A;
   A.h = H->d;
@@ -230,6 +229,7 @@ extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, c
   A.sess_out = d_sess_out;
   A.step_ns = d_step_ns;
   A.ctl = d_ctl;
+  A.free_stack = d_free_stack;
   A.steps = steps;
   A.seed = seed;
   A.cap_blocks = cap_blocks;

@@ -31,7 +31,8 @@ class ServeRun:
         self.tables = torch.empty(n_slots * max_blocks, dtype=torch.int64, device=dev)
         self.sess_out = torch.empty(5 * max(self.n, 1), dtype=torch.int64, device=dev)
         self.step_ns = torch.zeros(steps, dtype=torch.int64, device=dev)
-        self.ctl = torch.zeros(8, dtype=torch.int64, device=dev)
+        self.ctl = torch.zeros(9, dtype=torch.int64, device=dev)
+        self.free_stack = torch.empty(n_slots, dtype=torch.int32, device=dev)
 
     def run(self, heap, cap_blocks: int, blocks_per_sm: int = 0) -> float:
         """One call of the device loop; returns its duration in ms (CUDA events)."""
@@ -42,7 +43,8 @@ class ServeRun:
         st = B.load().ouro_serve(
             C.c_void_p(heap.h), B._ptr(self.d_arrive), B._ptr(self.d_blocks), self.n, self.n_slots,
             self.max_blocks, B._ptr(self.slot_session), B._ptr(self.slot_k), B._ptr(self.slot_acc),
-            B._ptr(self.tables), B._ptr(self.sess_out), B._ptr(self.step_ns), B._ptr(self.ctl), self.steps,
+            B._ptr(self.tables), B._ptr(self.sess_out), B._ptr(self.step_ns), B._ptr(self.ctl),
+            B._ptr(self.free_stack), self.steps,
             self.seed, cap_blocks, self.block_bytes, blocks_per_sm, B._stream(None))
         B._check("ouro_serve", st)
         b.record(s)

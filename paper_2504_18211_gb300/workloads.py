@@ -62,3 +62,20 @@ def serving_workload(steps: int = 2000, rate: float = 2000.0, dt: float = 0.01, 
     size = r.lognormal(np.log(median_bytes), sigma, n)
     blocks = np.clip(np.ceil(size / block_bytes), 1, max_blocks).astype(np.uint32)
     return arrive, blocks
+
+
+def graph_workload(n_vertices: int = 1 << 20, n_edges: int = 1 << 24, alpha: float = 2.1,
+                   seed: int = SEED_BASE + 2):
+    """Directed edges whose endpoints follow a power law over a seeded
+    permutation of the vertices.  alpha is read as the degree-distribution
+    exponent, so the rank-frequency exponent is s = 1 / (alpha - 1).
+    Returns (src, dst) uint32 arrays."""
+    r = rng(seed)
+    s = 1.0 / (alpha - 1.0)
+    w = np.arange(1, n_vertices + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    perm = r.permutation(n_vertices).astype(np.uint32)
+    src = perm[np.minimum(np.searchsorted(cdf, r.random(n_edges), side="right"), n_vertices - 1)]
+    dst = perm[np.minimum(np.searchsorted(cdf, r.random(n_edges), side="right"), n_vertices - 1)]
+    return src.astype(np.uint32), dst.astype(np.uint32)
