@@ -280,9 +280,14 @@ def run_serving(args):
                 np.full(int(blocks[s]), block, np.uint32), (run.seed + int(s)) & 0xFFFFFFFF, 1)) for s in sample)
         lat = r["step_us"]
         ops = r["mallocs"] + r["frees"]
+        ph = {k: {"p50": round(float(np.percentile(v, 50)), 1), "p99": round(float(np.percentile(v, 99)), 1),
+                  "max": round(float(v.max()), 1), "total_ms": round(float(v.sum()) / 1e3, 1)}
+              for k, v in r["phases"].items()}
+        slow = np.argsort(lat)[-5:][::-1]
         res[variant] = {"ms": round(ms, 2), "mops": round(ops / (ms / 1e3) / 1e6, 1),
                         "step_us_p50": round(float(np.percentile(lat, 50)), 1),
                         "step_us_p99": round(float(np.percentile(lat, 99)), 1),
+                        "phases": ph, "slowest_steps": [int(i) + 1 for i in slow],
                         "mallocs": r["mallocs"], "frees": r["frees"], "failed": r["failed"],
                         "admitted": int((r["admit"] >= 0).sum()), "completed": int((r["done"] >= 0).sum()),
                         "peak_committed_blocks_cap": cap,

@@ -267,7 +267,8 @@ ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
  *   d_slot_session n_slots ints, d_slot_k n_slots, d_slot_acc 3*n_slots,
  *   d_tables n_slots*max_blocks pointers, d_sess_out 5*n_sessions words
  *   (xor, sum, mismatches, admit step, done step; all ones if never),
- *   d_step_ns `steps` %globaltimer stamps, d_ctl 9 words (barrier state, next
+ *   d_step_ns 3*`steps` %globaltimer stamps (after admission, growth and
+ *   completion of each step), d_ctl 9 words (barrier state, next
  *   arrival, committed blocks, error flag, mallocs, frees, failed mallocs,
  *   free-slot stack top), d_free_stack n_slots slot ids.
  * ENOTSUP if the device cannot launch cooperative kernels.  A grid barrier

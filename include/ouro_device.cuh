@@ -267,7 +267,8 @@ __device__ inline unsigned spare_pop(const ouro_heap_dev &h, int c) {
  * the heap.  Every slot starts empty for its own position. */
 __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) {
   unsigned x = spare_pop(h, c);
-  if (x == OURO_NIL) {
+  const bool fresh = x == OURO_NIL;
+  if (fresh) {
     chunk_range r = take_chunks(h, 1);
     if (r.k1 + r.k2 == 0) return OURO_NIL;
     x = range_chunk(h, r, 0);
@@ -276,11 +277,24 @@ __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) 
   }
   ouro_seg *s = seg_of(h, x);
   s->done = 0;
-  unsigned long long *cells = seg_cells(h, x);
-  const unsigned long long p0 = (unsigned long long)idx * h.seg_cap;
-  for (unsigned i = 0; i < h.seg_cap; i += 2) {
-    ulonglong2 v = make_ulonglong2(slot(p0 + i, 0), slot(p0 + i + 1, 0));
-    *reinterpret_cast<ulonglong2 *>(cells + i) = v;   /* seg_cap is even, cells 16-B aligned */
+  /* A segment recycled from the spare stack always serves a higher index, so
+   * its stale slots hold sequences below every new position: single-use list
+   * slots read "sequence behind position" as empty, and the slots need no
+   * rewrite -- unless the index jumped so far that 32-bit sequences could
+   * wrap.  A chunk fresh from the heap is initialised. */
+  bool init = fresh;
+  if (!fresh) {
+    const unsigned old_idx = hi32(s->link);
+    const int ahead = (int)(idx - old_idx);
+    init = ahead <= 0 || (unsigned long long)ahead * h.seg_cap >= (1ull << 30);
+  }
+  if (init) {
+    unsigned long long *cells = seg_cells(h, x);
+    const unsigned long long p0 = (unsigned long long)idx * h.seg_cap;
+    for (unsigned i = 0; i < h.seg_cap; i += 2) {
+      ulonglong2 v = make_ulonglong2(slot(p0 + i, 0), slot(p0 + i + 1, 0));
+      *reinterpret_cast<ulonglong2 *>(cells + i) = v;   /* seg_cap is even, cells 16-B aligned */
+    }
   }
   s->link = pack(idx, OURO_NIL);
   __threadfence();
@@ -430,7 +444,7 @@ __device__ __forceinline__ unsigned long long *slot_at(const ouro_heap_dev &h, i
  * 1: the consumer gave the position up (caller re-queues the item);
  * -1: an earlier lap never drained (timeout). */
 __device__ inline int put_at(const ouro_heap_dev &h, unsigned long long *cell, unsigned long long pos,
-                             unsigned item, bool null_marker) {
+                             unsigned item, bool null_marker, bool single_use = false) {
   const unsigned long long want = null_marker ? slot(pos + 2, 0) : slot(pos + 1, item);
   unsigned long long expect = slot(pos, 0);
   unsigned ns = h.backoff_min_ns;
@@ -438,7 +452,7 @@ __device__ inline int put_at(const ouro_heap_dev &h, unsigned long long *cell, u
     unsigned long long old = cas_rel(cell, expect, want);
     if (old == expect) return 0;
     int d = slot_d(old, pos);
-    if (d == 0) { expect = old; continue; }   /* empty slot with a posted value */
+    if (d == 0 || (single_use && d < 0)) { expect = old; continue; }   /* empty (posted value / stale lap) */
     if (d >= 3) return 1;
     __nanosleep(ns);
     ns = min(ns * 2, h.backoff_max_ns);
@@ -478,7 +492,7 @@ __device__ inline int give_up(const ouro_heap_dev &h, int c, unsigned long long 
       if (!VL) st_rlx(cell, retired);
       return d;
     }
-    if (d != 0) return 0;
+    if (d > 0 || (!VL && d != 0)) return 0;     /* list slots: behind the position is empty too */
     if (cas_ar(cell, v, retired) == v) return 3;
   }
   return 0;
@@ -492,7 +506,7 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
     unsigned long long t = atomicAdd(&q->tail.v, 1ull);
     unsigned long long *cell = slot_at<VL>(h, c, t, true);
     if (!cell) return;   /* error already recorded */
-    int rc = put_at(h, cell, t, item, false);
+    int rc = put_at(h, cell, t, item, false, VL);
     if (VL) vl_event(h, c, cell, 1);
     if (rc == 0) return;
     if (rc < 0) return;
@@ -572,7 +586,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
         const unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
         item = (x << ppc_log) | (unsigned)(i & (ppc - 1));
         cell = slot_at<VL>(h, c, t0 + i, true);
-        if (cell) rc = put_at(h, cell, t0 + i, item, false);   /* no slot: queue storage exhausted (recorded) */
+        if (cell) rc = put_at(h, cell, t0 + i, item, false, VL);   /* no slot: queue storage exhausted (recorded) */
       }
       if (VL) vl_event_warp(h, c, cell, act, vmask);
       if (act && rc == 1) push_one<VL>(h, c, item);
@@ -594,7 +608,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
       const unsigned long long i = i0 + rk;
       const bool act = i < dn;
       unsigned long long *cell = act ? slot_at<VL>(h, c, dt + i, true) : nullptr;
-      if (cell) put_at(h, cell, dt + i, 0, true);
+      if (cell) put_at(h, cell, dt + i, 0, true, VL);
       if (VL) vl_event_warp(h, c, cell, act, vmask);
     }
   }
@@ -723,7 +737,7 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
   } else {
     cell = ring_slot(h, cls, t);
   }
-  int rc = cell ? put_at(h, cell, t, item, false) : 0;   /* no slot: queue storage exhausted, page lost (recorded) */
+  int rc = cell ? put_at(h, cell, t, item, false, VL) : 0;   /* no slot: queue storage exhausted, page lost (recorded) */
   if (VL) vl_event_warp(h, cls, cell, true, vmask);
   if (rc == 1) {
     stat_add(h, cls, OURO_ST_REPUSH, 1);
@@ -873,7 +887,7 @@ __device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int o
       const unsigned i = rk + (unsigned)r * nl;
       if (i >= D || !cell[r]) continue;
       const bool isnull = item[r] == 0xffffffffu;
-      int rc = put_at(h, cell[r], t + i, isnull ? 0 : item[r], isnull);
+      int rc = put_at(h, cell[r], t + i, isnull ? 0 : item[r], isnull, VL);
       if (VL) vl_event(h, c, cell[r], 1);   /* planned positions: at most 8 per lane */
       if (rc == 1 && !isnull) {   /* its group gave up: hand the reserved pages back */
         const unsigned x = OURO_CQ_ID(item[r]);
@@ -909,7 +923,7 @@ __device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int o
       for (unsigned long long i = rk; i < dn; i += nl) {
         unsigned long long *cl = slot_at<VL>(h, c, dt + i, true);
         if (!cl) continue;
-        put_at(h, cl, dt + i, 0, true);
+        put_at(h, cl, dt + i, 0, true, VL);
         if (VL) vl_event(h, c, cl, 1);
       }
       break;
@@ -1019,9 +1033,10 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
         if (!posted) {
           if (!cell && VL) cell = vl_slot(h, cls, pos, true);
           if (cell) {
-            const unsigned long long e = slot(pos, 0);
+            const unsigned long long e = ld_acq(cell);
+            const int d = slot_d(e, pos);
             posted = true;
-            cas_ar(cell, e, slot(pos, need));
+            if (d == 0 || (VL && d < 0)) cas_ar(cell, e, slot(pos, need));
           }
         }
       }

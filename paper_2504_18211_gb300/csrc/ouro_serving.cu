@@ -40,7 +40,7 @@ struct serve_args {
   unsigned long long *tables;    /* n_slots x max_blocks block pointers */
   /* results */
   unsigned long long *sess_out;  /* per session: xor, sum, mismatches, admit step, done step (u64 each) */
-  unsigned long long *step_ns;   /* per step: %globaltimer at its end */
+  unsigned long long *step_ns;   /* per step: %globaltimer after admission, growth and completion (3 words) */
   unsigned long long *ctl;       /* [0] barrier count, [1] barrier generation, [2] next arrival,
                                     [3] committed blocks, [4] error, [5] mallocs, [6] frees, [7] failed,
                                     [8] free-slot stack top */
@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
       __threadfence();
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[3 * step] = globaltimer();
     /* 2. growth: one session per warp: lane 0 allocates, the warp writes and
      *    reads back the block */
     for (uint32_t slot = warp; slot < A.n_slots; slot += nwarps) {
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
       }
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[3 * step + 1] = globaltimer();
     /* 3. completion: a warp per finished session frees its blocks */
     for (uint32_t slot = warp; slot < A.n_slots; slot += nwarps) {
       const int sess = A.slot_session[slot];
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
       __syncwarp();
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[step] = globaltimer();
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[3 * step + 2] = globaltimer();
   }
 }
 

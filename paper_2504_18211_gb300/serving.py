@@ -30,7 +30,7 @@ class ServeRun:
         self.slot_acc = torch.empty(3 * n_slots, dtype=torch.int64, device=dev)
         self.tables = torch.empty(n_slots * max_blocks, dtype=torch.int64, device=dev)
         self.sess_out = torch.empty(5 * max(self.n, 1), dtype=torch.int64, device=dev)
-        self.step_ns = torch.zeros(steps, dtype=torch.int64, device=dev)
+        self.step_ns = torch.zeros(3 * steps, dtype=torch.int64, device=dev)
         self.ctl = torch.zeros(9, dtype=torch.int64, device=dev)
         self.free_stack = torch.empty(n_slots, dtype=torch.int32, device=dev)
 
@@ -54,14 +54,17 @@ class ServeRun:
     def results(self) -> dict:
         so = self.sess_out.cpu().numpy().view(np.uint64).reshape(-1, 5)[: self.n]
         ctl = self.ctl.cpu().numpy().view(np.uint64)
-        ns = self.step_ns.cpu().numpy().view(np.uint64).astype(np.int64)
-        lat = np.diff(ns) / 1e3 if ns.size > 1 else np.zeros(0)
+        ns = self.step_ns.cpu().numpy().view(np.uint64).astype(np.int64).reshape(-1, 3)
+        ends = ns[:, 2]
+        lat = np.diff(ends) / 1e3 if ends.size > 1 else np.zeros(0)
+        phases = {"admit_us": (ns[1:, 0] - ends[:-1]) / 1e3, "grow_us": (ns[1:, 1] - ns[1:, 0]) / 1e3,
+                  "complete_us": (ns[1:, 2] - ns[1:, 1]) / 1e3}
         never = np.uint64(0xFFFFFFFFFFFFFFFF)
         return {"xor": so[:, 0], "sum": so[:, 1], "mism": so[:, 2],
                 "admit": np.where(so[:, 3] == never, -1, so[:, 3].astype(np.int64)),
                 "done": np.where(so[:, 4] == never, -1, so[:, 4].astype(np.int64)),
                 "mallocs": int(ctl[5]), "frees": int(ctl[6]), "failed": int(ctl[7]), "error": int(ctl[4]),
-                "step_us": lat}
+                "step_us": lat, "phases": phases}
 
 
 def model_schedule(arrive: np.ndarray, blocks: np.ndarray, steps: int, n_slots: int, cap_blocks: int):
