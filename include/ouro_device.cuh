@@ -522,7 +522,7 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
  * heap (or the page-array capacity) is exhausted, the remaining debt slots
  * get the null marker. */
 template <int V>
-__device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
+__device__ __noinline__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
   constexpr bool VL = (V == OURO_PAGE_VLIST);
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
@@ -576,20 +576,39 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
     __threadfence();
     __syncwarp(vmask);
     const unsigned long long total = (unsigned long long)m << ppc_log;
-    for (unsigned long long i0 = 0; i0 < total; i0 += nl) {
-      const unsigned long long i = i0 + rk;
-      const bool act = i < total;
-      unsigned long long *cell = nullptr;
-      int rc = 0;
-      unsigned item = 0;
-      if (act) {
-        const unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
-        item = (x << ppc_log) | (unsigned)(i & (ppc - 1));
-        cell = slot_at<VL>(h, c, t0 + i, true);
-        if (cell) rc = put_at(h, cell, t0 + i, item, false, VL);   /* no slot: queue storage exhausted (recorded) */
+    /* FILL positions per lane per round: their first compare-and-swaps are
+     * issued back to back (independent), then checked; a slot that was not
+     * plainly empty falls back to put_at */
+    constexpr int FILL = 8;
+    for (unsigned long long i0 = 0; i0 < total; i0 += (unsigned long long)nl * FILL) {
+      unsigned long long *cell[FILL];
+      unsigned item[FILL];
+      unsigned long long got[FILL];
+#pragma unroll
+      for (int f = 0; f < FILL; ++f) {
+        const unsigned long long i = i0 + (unsigned long long)f * nl + rk;
+        cell[f] = nullptr;
+        item[f] = 0;
+        if (i < total) {
+          const unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
+          item[f] = (x << ppc_log) | (unsigned)(i & (ppc - 1));
+          cell[f] = slot_at<VL>(h, c, t0 + i, true);      /* null: queue storage exhausted (recorded) */
+        }
       }
-      if (VL) vl_event_warp(h, c, cell, act, vmask);
-      if (act && rc == 1) push_one<VL>(h, c, item);
+#pragma unroll
+      for (int f = 0; f < FILL; ++f) {
+        const unsigned long long p = t0 + i0 + (unsigned long long)f * nl + rk;
+        got[f] = cell[f] ? cas_rel(cell[f], slot(p, 0), slot(p + 1, item[f])) : 0;
+      }
+#pragma unroll
+      for (int f = 0; f < FILL; ++f) {
+        const unsigned long long i = i0 + (unsigned long long)f * nl + rk;
+        const unsigned long long p = t0 + i;
+        int rc = 0;
+        if (cell[f] && got[f] != slot(p, 0)) rc = put_at(h, cell[f], p, item[f], false, VL);
+        if (VL) vl_event_warp(h, c, cell[f], i < total, vmask);
+        if (cell[f] && rc == 1) push_one<VL>(h, c, item[f]);
+      }
     }
   }
   if (exhausted) {
@@ -782,7 +801,7 @@ __device__ inline void chunk_push(const ouro_heap_dev &h, int c, unsigned x) {
 
 /* Called by every lane of vmask; lane `owner` holds the carve lock of class c. */
 template <int V>
-__device__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
+__device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
   constexpr bool VL = (V == OURO_CHUNK_VLIST);
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
