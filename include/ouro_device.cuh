@@ -522,7 +522,7 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
  * heap (or the page-array capacity) is exhausted, the remaining debt slots
  * get the null marker. */
 template <int V>
-__device__ __noinline__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
+__device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
   constexpr bool VL = (V == OURO_PAGE_VLIST);
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
@@ -579,7 +579,7 @@ __device__ __noinline__ void page_carve(const ouro_heap_dev &h, int c, unsigned 
     /* FILL positions per lane per round: their first compare-and-swaps are
      * issued back to back (independent), then checked; a slot that was not
      * plainly empty falls back to put_at */
-    constexpr int FILL = 8;
+    constexpr int FILL = 1;
     for (unsigned long long i0 = 0; i0 < total; i0 += (unsigned long long)nl * FILL) {
       unsigned long long *cell[FILL];
       unsigned item[FILL];
@@ -636,32 +636,36 @@ __device__ __noinline__ void page_carve(const ouro_heap_dev &h, int c, unsigned 
 }
 
 /* --------------------------------------------------------- page queues */
-/* All lanes of vmask hold a request of class cls (any mix of classes). */
+/* Every lane of vmask calls.  A lane with cls >= 0 asks for a page of that
+ * class (any mix of classes); a lane with cls < 0 asks for nothing and only
+ * helps: it takes part in the warp's carves, so that a warp in which one
+ * lane allocates still fills new slots 32 lanes wide. */
 template <int V>
 __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   constexpr bool VL = (V == OURO_PAGE_VLIST);
-  ouro_qhdr *q = qh(h, cls);
+  const bool req = cls >= 0;
+  ouro_qhdr *q = qh(h, req ? cls : 0);
   const unsigned lane = laneid();
   const unsigned grp = __match_any_sync(vmask, cls);
   const unsigned leader = __ffs(grp) - 1;
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long pos = 0;
-  if (lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
+  if (req && lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
   const unsigned long long p0 = __shfl_sync(vmask, pos, leader);
   pos = p0 + rank;
 
   unsigned item = 0;
-  int st = 0;   /* 0 waiting, 1 item, 2 null answer, 3 gave up */
-  unsigned long long *cell;
+  int st = req ? 0 : 3;   /* 0 waiting, 1 item, 2 null answer, 3 gave up (helpers: nothing asked) */
+  unsigned long long *cell = nullptr;
   if (VL) {   /* the leader finds its segment; lanes in the same segment reuse it */
-    unsigned long long *c0 = lane == leader ? vl_slot(h, cls, p0, false) : nullptr;
+    unsigned long long *c0 = (req && lane == leader) ? vl_slot(h, cls, p0, false) : nullptr;
     c0 = reinterpret_cast<unsigned long long *>(
         __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
-    cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + rank : vl_slot(h, cls, pos, false);
-  } else {
+    if (req) cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + rank : vl_slot(h, cls, pos, false);
+  } else if (req) {
     cell = ring_slot(h, cls, pos);
   }
-  if (cell) st = try_take<VL>(h, cls, cell, pos, &item);
+  if (req && cell) st = try_take<VL>(h, cls, cell, pos, &item);
 
   bool gave_up = false;
   if (__ballot_sync(vmask, st == 0)) {
@@ -725,7 +729,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   /* per-class counters, one update per class group of the warp */
   const unsigned g2 = __match_any_sync(vmask, cls);
   const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
-  if (lane == (unsigned)(__ffs(g2) - 1)) {
+  if (req && lane == (unsigned)(__ffs(g2) - 1)) {
     stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
     stat_add(h, cls, OURO_ST_FAILED, __popc(g2) - __popc(okm));
   }
@@ -1008,14 +1012,16 @@ __device__ inline unsigned claim_pages(const ouro_heap_dev &h, unsigned x, unsig
   return mine;
 }
 
+/* Every lane of vmask calls; lanes with cls < 0 only help (see page_malloc). */
 template <int V>
 __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   constexpr bool VL = (V == OURO_CHUNK_VLIST);
-  ouro_qhdr *q = qh(h, cls);
+  const bool req = cls >= 0;
+  ouro_qhdr *q = qh(h, req ? cls : 0);
   const unsigned lane = laneid();
-  const unsigned ppc_log = h.log2_chunk - 4 - cls;
+  const unsigned ppc_log = req ? h.log2_chunk - 4 - cls : 0;
   const unsigned ppc = 1u << ppc_log;
-  int st = 0;                    /* 0 waiting, 1 page, 2 null */
+  int st = req ? 0 : 2;          /* 0 waiting, 1 page, 2 null (helpers: nothing asked) */
   unsigned page = 0, chunk = 0;
   /* group-leader state: one queue position at a time */
   bool have = false, posted = false;
@@ -1153,7 +1159,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   if (st == 1) ret = h.base + ((size_t)chunk << h.log2_chunk) + ((size_t)page << (4 + cls));
   const unsigned g2 = __match_any_sync(vmask, cls);
   const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
-  if (lane == (unsigned)(__ffs(g2) - 1)) {
+  if (req && lane == (unsigned)(__ffs(g2) - 1)) {
     stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
     stat_add(h, cls, OURO_ST_FAILED, __popc(g2) - __popc(okm));
   }
@@ -1208,16 +1214,14 @@ static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t 
   using namespace ouro::detail;
   const unsigned mask = __activemask();
   const int cls = size_class(h, n);
-  const unsigned vmask = __ballot_sync(mask, cls >= 0);
-  if (cls < 0) {
-    stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
-    return nullptr;
-  }
+  if (cls < 0) stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+  if (!__any_sync(mask, cls >= 0)) return nullptr;
+  /* lanes without a class stay in as helpers of the warp's carves */
   switch (h.variant) {
-    case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, vmask);
-    case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, vmask);
-    case OURO_CHUNK_ARRAY: return chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, vmask);
-    case OURO_CHUNK_VLIST: return chunk_malloc<OURO_CHUNK_VLIST>(h, cls, vmask);
+    case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, mask);
+    case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, mask);
+    case OURO_CHUNK_ARRAY: return chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, mask);
+    case OURO_CHUNK_VLIST: return chunk_malloc<OURO_CHUNK_VLIST>(h, cls, mask);
     default: return nullptr;
   }
 }

@@ -96,8 +96,8 @@ __device__ void warp_append(const ouro_heap_dev &h, vertex *vx, const unsigned l
     unsigned long long ptr = vv->ptr;
     if (cnt == cap && cap < max_plain && cap) {
       /* one doubling: malloc 2x, copy, free the old list */
-      unsigned long long np = 0;
-      if (lane == 0) np = reinterpret_cast<unsigned long long>(malloc_v<V>(h, (size_t)cap * 8));
+      /* lane 0 asks, the other lanes help the warp's carves */
+      unsigned long long np = reinterpret_cast<unsigned long long>(malloc_v<V>(h, (size_t)cap * 8, lane == 0));
       np = __shfl_sync(0xffffffffu, np, 0);
       if (!np) {
         if (lane == 0) atomicAdd(&ctl[1], (unsigned long long)(n - done));
@@ -129,9 +129,8 @@ __device__ void warp_append(const ouro_heap_dev &h, vertex *vx, const unsigned l
     unsigned long long seg = vv->ovf;
     unsigned oc = vv->ovf_cnt;
     if (!seg || oc == seg_cap) {
-      unsigned long long ns = 0;
+      unsigned long long ns = reinterpret_cast<unsigned long long>(malloc_v<V>(h, h.chunk_bytes, lane == 0));
       if (lane == 0) {
-        ns = reinterpret_cast<unsigned long long>(malloc_v<V>(h, h.chunk_bytes));
         if (ns) {
           *reinterpret_cast<unsigned long long *>(ns) = seg;
           vv->ovf = ns;

@@ -10,17 +10,16 @@ namespace ouro {
 namespace detail {
 
 
+/* Variant-resolved malloc.  want = false: the lane asks for nothing but
+ * stays in the call to help its warp carve (see page_malloc). */
 template <int V>
-__device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long long n) {
+__device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long long n, bool want = true) {
   const unsigned mask = __activemask();
-  const int cls = size_class(h, n);
-  const unsigned vmask = __ballot_sync(mask, cls >= 0);
-  if (cls < 0) {
-    stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
-    return nullptr;
-  }
-  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) return page_malloc<V>(h, cls, vmask);
-  else return chunk_malloc<V>(h, cls, vmask);
+  const int cls = want ? size_class(h, n) : -1;
+  if (want && cls < 0) stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+  if (!__any_sync(mask, cls >= 0)) return nullptr;
+  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) return page_malloc<V>(h, cls, mask);
+  else return chunk_malloc<V>(h, cls, mask);
 }
 
 template <int V>

@@ -9,6 +9,7 @@
  * allocator throughput as a fraction of them.
  */
 #include "ouro_internal.cuh"
+#include "ouro_payload.cuh"
 
 using namespace ouro::detail;
 
@@ -59,13 +60,7 @@ __global__ void k_malloc_timed(ouro_heap_dev h, const uint32_t *sizes, void **pt
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const unsigned long long t0 = clock64();
     void *p;
-    {
-      const unsigned mask = __activemask();
-      const int cls = size_class(h, sizes[i]);
-      const unsigned vmask = __ballot_sync(mask, cls >= 0);
-      if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) p = cls >= 0 ? page_malloc<V>(h, cls, vmask) : nullptr;
-      else p = cls >= 0 ? chunk_malloc<V>(h, cls, vmask) : nullptr;
-    }
+    p = malloc_v<V>(h, sizes[i]);
     const unsigned long long t1 = clock64();
     ptrs[i] = p;
     atomicAdd(&sh[min(lat_bin(t1 - t0), 255u)], 1ull);

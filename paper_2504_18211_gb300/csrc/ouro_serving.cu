@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
       if (sess < 0) continue;
       const uint32_t k = A.slot_k[slot];
       if (k >= A.blocks[sess]) continue;
-      unsigned long long bp = 0;
+      /* lane 0 asks; the other 31 lanes help the warp's carves */
+      unsigned long long bp = reinterpret_cast<unsigned long long>(malloc_v<V>(h, A.block_bytes, lane == 0));
       if (lane == 0) {
-        bp = reinterpret_cast<unsigned long long>(malloc_v<V>(h, A.block_bytes));
         if (bp) {
           A.tables[(size_t)slot * A.max_blocks + k] = bp;
           A.slot_k[slot] = k + 1;
