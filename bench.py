@@ -232,9 +232,15 @@ def run_batching(args):
         got = run.checks()
         st = heap.stats()
         run.close()
+    with P.Heap(heap_bytes, 8192, args.variant, staging=True) as heap:
+        ms = run.time(heap, "persistent", reps=2)
+        res["forms"]["persistent_staged"] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
+        got_staged = run.checks()
+        st = heap.stats() if st["error_bits"] == 0 else st
     o = offs.astype(np.int64)
     want = [oracle.expected_checksums(sizes[o[b]:o[b + 1]], run.seed + b, 1) for b in range(offs.size - 1)]
-    res["verified"] = all(g == dict(w, nulls=0, mismatches=0) for g, w in zip(got, want)) and st["error_bits"] == 0
+    res["verified"] = all(g == dict(w, nulls=0, mismatches=0) and gs == g for g, gs, w in zip(got, got_staged, want)) \
+        and st["error_bits"] == 0
     sub_sizes, sub_offs = sizes[: int(offs[16])], offs[:17]
     tune_run = BT.BatchRun(sub_sizes, sub_offs)
     best, table = BT.autotune(P.Heap, tune_run, heap_bytes)
@@ -524,6 +530,15 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
                          "alloc_free_mops": round(2 * n / ((pl2["malloc"] + pl2["free"]) / 1e3) / 1e6, 1),
                          "per_launch_ms": {k: round(x, 4) for k, x in pl2.items()}, "verified": ok}
     ex["variants"] = others
+
+    # ---- shared-memory staging of freed pages (page queues)
+    with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=True) as h3:
+        o3 = torch.zeros(5, dtype=torch.int64, device="cuda")
+        for _ in range(3):
+            h3.round_fused(sizes, SEED, 1, out=o3)
+        sms = timed(torch, stream, lambda: h3.round_fused(sizes, SEED, 1, out=o3), 5)
+        ok3 = P.check_to_dict(o3)["mismatches"] == 0 and h3.stats()["error_bits"] == 0
+        ex["staging"] = {"fused_mops": round(2 * n / (sms / 1e3) / 1e6, 1), "ms": round(sms, 4), "verified": ok3}
 
     # ---- malloc latency histogram (warm heap, malloc-only batch)
     hist = torch.zeros(256, dtype=torch.int64, device="cuda")

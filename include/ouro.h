@@ -71,7 +71,8 @@ typedef struct {
   uint32_t max_carve;             /* chunks one carve may take at once (default 65536) */
   uint64_t array_queue_capacity;  /* page-array item limit per class (default 1<<23) */
   uint32_t checked;               /* page queues: track live pages to detect double frees */
-  uint32_t reserved;
+  uint32_t staging;               /* page queues: the library's fused / persistent kernels stage
+                                     freed pages per warp in shared memory (ouro_block_ctx) */
 } ouro_options;
 
 /* Device view of a heap, passed BY VALUE to kernels that call ouro_malloc /
@@ -83,7 +84,7 @@ typedef struct {
   unsigned int chunk_bytes, log2_chunk, n_classes, variant;
   unsigned int seg_cap, words_per_chunk;
   unsigned int spin_limit, backoff_min_ns, backoff_max_ns, max_carve;
-  unsigned int checked, pad0;
+  unsigned int checked, staging;
   void *qhdr;                          /* per-class queue headers */
   unsigned long long *cells;           /* array variants: every class ring, back to back */
   unsigned long long ring_off[OURO_MAX_CLASSES];

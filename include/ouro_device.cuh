@@ -1207,6 +1207,138 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
 }  // namespace detail
 }  // namespace ouro
 
+/* ------------------------------------------------- block staging (page queues) */
+/* Shared-memory staging of freed pages: every warp of a block owns, per size
+ * class, a stack of up to OURO_STAGE_CAP page ids.  A staged free pushes the
+ * page id there instead of into the class queue; a later staged malloc of
+ * the same class in the same warp pops it, with no global atomic and no
+ * queue slot traffic.  Stacks are warp-private, so no synchronisation beyond
+ * __syncwarp is needed.  ouro_block_end pushes what is left back to the
+ * class queues; a kernel must call it before it exits.  Page queues only:
+ * with chunk queues the staged calls go straight to the heap. */
+#define OURO_STAGE_CAP 16
+template <int WARPS>
+struct ouro_block_ctx {
+  unsigned char cnt[WARPS][OURO_MAX_CLASSES];
+  unsigned ids[WARPS][OURO_MAX_CLASSES][OURO_STAGE_CAP];
+};
+
+namespace ouro {
+namespace detail {
+
+/* staged malloc for page queues; every lane of the warp's call mask calls */
+template <int V, int WARPS>
+__device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, unsigned long long n, bool want) {
+  const unsigned mask = __activemask();
+  const unsigned lane = laneid(), w = threadIdx.x >> 5;
+  int cls = want ? size_class(h, n) : -1;
+  if (want && cls < 0) stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+  const unsigned g = __match_any_sync(mask, cls);
+  const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
+  unsigned have = 0, take = 0;
+  if (cls >= 0 && lane == leader) {
+    have = ctx.cnt[w][cls];
+    take = min(have, k);
+    ctx.cnt[w][cls] = (unsigned char)(have - take);
+  }
+  have = __shfl_sync(mask, have, leader);
+  take = __shfl_sync(mask, take, leader);
+  void *res = nullptr;
+  if (cls >= 0 && rank < take) {
+    const unsigned item = ctx.ids[w][cls][have - 1 - rank];
+    if (h.checked) {
+      const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
+      const unsigned bit = 1u << (pg & 31);
+      const unsigned old = atomicAnd(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], ~bit);
+      if (!(old & bit)) set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_CHECKED);
+    }
+    res = h.base + ((size_t)item << (4 + cls));
+  }
+  if (cls >= 0 && lane == leader && take) stat_add(h, cls, OURO_ST_MALLOC, take);
+  __syncwarp(mask);
+  const int rest = (cls >= 0 && rank >= take) ? cls : -1;   /* served lanes help the rest */
+  if (__any_sync(mask, rest >= 0)) {
+    void *p = page_malloc<V>(h, rest, mask);
+    if (rest >= 0) res = p;
+  }
+  return res;
+}
+
+/* staged free for page queues; every lane of the warp's call mask calls */
+template <int V, int WARPS>
+__device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
+  const unsigned mask = __activemask();
+  const unsigned lane = laneid(), w = threadIdx.x >> 5;
+  unsigned item = 0;
+  int cls = -1;
+  if (p) {
+    cls = locate(h, p, &item);
+    if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
+    else if (h.checked) {
+      const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
+      const unsigned bit = 1u << (pg & 31);
+      __threadfence();
+      const unsigned old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bit);
+      if (old & bit) {
+        set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_DOUBLE);
+        cls = -1;
+      }
+    }
+  }
+  const unsigned g = __match_any_sync(mask, cls);
+  const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
+  unsigned have = 0, take = 0;
+  if (cls >= 0 && lane == leader) {
+    have = ctx.cnt[w][cls];
+    take = min(OURO_STAGE_CAP - have, k);
+    ctx.cnt[w][cls] = (unsigned char)(have + take);
+    if (take) stat_add(h, cls, OURO_ST_FREE, take);
+  }
+  have = __shfl_sync(mask, have, leader);
+  take = __shfl_sync(mask, take, leader);
+  if (cls >= 0 && rank < take) ctx.ids[w][cls][have + rank] = item;
+  __syncwarp(mask);
+  const unsigned rest = __ballot_sync(mask, cls >= 0 && rank >= take);
+  if (rest && ((rest >> lane) & 1)) page_free<V>(h, cls, item, rest);
+}
+
+}  // namespace detail
+}  // namespace ouro
+
+/* Every thread of the block calls (clears the stacks, then __syncthreads). */
+template <int WARPS>
+__device__ void ouro_block_begin(ouro_block_ctx<WARPS> &ctx) {
+  for (unsigned i = threadIdx.x; i < WARPS * OURO_MAX_CLASSES; i += blockDim.x)
+    (&ctx.cnt[0][0])[i] = 0;
+  __syncthreads();
+}
+
+/* Every thread of the block calls: each warp returns its staged pages to
+ * the class queues, then __syncthreads. */
+template <int V, int WARPS>
+__device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h) {
+  using namespace ouro::detail;
+  const unsigned lane = laneid(), w = threadIdx.x >> 5;
+  __syncwarp();
+  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) {
+    for (unsigned c = 0; c < h.n_classes; ++c) {
+      const unsigned n = ctx.cnt[w][c];
+      if (!n) continue;
+      const bool mine = lane < n;
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      if (mine) page_free<V>(h, (int)c, ctx.ids[w][c][lane], m);
+      __syncwarp();
+      if (lane == 0) {
+        ctx.cnt[w][c] = 0;
+        /* these pages were counted as freed when they were staged */
+        stat_add(h, c, OURO_ST_FREE, 0ull - (unsigned long long)n);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 /* ------------------------------------------------------------- public API */
 /* Allocate n bytes from the heap; null when n is 0 or above one chunk, when
  * the heap is exhausted, or when a bounded wait ran out. */

@@ -24,11 +24,13 @@ namespace {
 
 constexpr unsigned TASK_REQ = 256;   /* requests per persistent task: 8 warp iterations */
 
-template <int V>
+template <int V, bool STAGE>
 __global__ void __launch_bounds__(256, 4)
 k_batches_persistent(ouro_heap_dev h, const uint32_t *sizes, const unsigned long long *offs,
                      const unsigned long long *task_offs, unsigned n_batches, uint32_t seed, int mode,
                      ouro_check *out, unsigned long long *work, unsigned long long n_tasks) {
+  __shared__ ouro_block_ctx<8> ctx;
+  if (STAGE) ouro_block_begin(ctx);
   const unsigned lane = laneid();
   for (;;) {
     unsigned long long task = 0;
@@ -52,18 +54,19 @@ k_batches_persistent(ouro_heap_dev h, const uint32_t *sizes, const unsigned long
       if (!__any_sync(0xffffffffu, active)) break;
       const uint32_t sz = active ? sizes[base + i] : 0;
       unsigned char *p = nullptr;
-      if (active) {
-        p = static_cast<unsigned char *>(malloc_v<V>(h, sz));
-        if (!p) nulls++;
-      }
+      if (STAGE) p = static_cast<unsigned char *>(stage_malloc_v<V>(ctx, h, sz, active));
+      else if (active) p = static_cast<unsigned char *>(malloc_v<V>(h, sz));
+      if (active && !p) nulls++;
       __syncwarp();
       warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed + b, mode, a);
       __syncwarp();
-      if (active) free_v<V>(h, p);
+      if (STAGE) stage_free_v<V>(ctx, h, p);
+      else if (active) free_v<V>(h, p);
       __syncwarp();
     }
     warp_flush(a, nulls, &out[b]);
   }
+  if (STAGE) ouro_block_end_v<V>(ctx, h);
 }
 
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -87,13 +90,23 @@ extern "C" ouro_status ouro_batches_persistent(ouro_heap *H, const uint32_t *d_s
   OURO_CUDA(cudaMemsetAsync(d_work, 0, 8, S(stream)));
   if (!n_tasks) return OURO_OK;
   int per_sm = 0;
-  OURO_DISPATCH(H->d.variant, ({
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<V>, 256, 0);
-    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
-    if (per_sm < 1) per_sm = 1;
-    k_batches_persistent<V><<<per_sm * ouro::host::sm_count(), 256, 0, S(stream)>>>(
-        H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
-  }));
+  if (H->d.staging) {
+    OURO_DISPATCH(H->d.variant, ({
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<V, true>, 256, 0);
+      if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+      if (per_sm < 1) per_sm = 1;
+      k_batches_persistent<V, true><<<per_sm * ouro::host::sm_count(), 256, 0, S(stream)>>>(
+          H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
+    }));
+  } else {
+    OURO_DISPATCH(H->d.variant, ({
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<V, false>, 256, 0);
+      if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+      if (per_sm < 1) per_sm = 1;
+      k_batches_persistent<V, false><<<per_sm * ouro::host::sm_count(), 256, 0, S(stream)>>>(
+          H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
+    }));
+  }
   OURO_LAUNCHED();
   return OURO_OK;
 }
@@ -102,10 +115,10 @@ extern "C" int ouro_batches_max_blocks_per_sm(const ouro_heap *H) {
   if (!H) return 0;
   int per_sm = 0;
   switch (H->d.variant) {
-    case OURO_PAGE_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_ARRAY>, 256, 0); break;
-    case OURO_PAGE_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_VLIST>, 256, 0); break;
-    case OURO_CHUNK_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_ARRAY>, 256, 0); break;
-    case OURO_CHUNK_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_VLIST>, 256, 0); break;
+    case OURO_PAGE_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_ARRAY, false>, 256, 0); break;
+    case OURO_PAGE_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_VLIST, false>, 256, 0); break;
+    case OURO_CHUNK_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_ARRAY, false>, 256, 0); break;
+    case OURO_CHUNK_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_VLIST, false>, 256, 0); break;
     default: break;
   }
   return per_sm;

@@ -127,7 +127,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   o.max_carve = 1u << 16;
   o.array_queue_capacity = 1ull << 23;
   o.checked = 0;
-  o.reserved = 0;
+  o.staging = 0;
   if (opt) {
     if (opt->spin_limit) o.spin_limit = opt->spin_limit;
     if (opt->backoff_min_ns) o.backoff_min_ns = opt->backoff_min_ns;
@@ -135,6 +135,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
     if (opt->max_carve) o.max_carve = opt->max_carve;
     if (opt->array_queue_capacity) o.array_queue_capacity = opt->array_queue_capacity;
     o.checked = opt->checked;
+    o.staging = opt->staging;
   }
   if (o.backoff_max_ns < o.backoff_min_ns) o.backoff_max_ns = o.backoff_min_ns;
 
@@ -157,6 +158,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   d.backoff_max_ns = o.backoff_max_ns;
   d.max_carve = o.max_carve;
   d.checked = o.checked ? 1u : 0u;
+  d.staging = (o.staging && is_page(variant)) ? 1u : 0u;
 
   /* ring sizes (array variants) */
   unsigned long long ring_total = 0;

@@ -47,10 +47,14 @@ __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, ui
   if (OP & PAY_CHECK) flush_acc(a, nulls, out);
 }
 
-/* one whole round per thread: malloc, write, read back, free */
-template <int V>
+/* one whole round per thread: malloc, write, read back, free.  STAGE: the
+ * warp's freed pages serve its next mallocs of the same class from shared
+ * memory (page queues, heap option `staging`). */
+template <int V, bool STAGE>
 __global__ void __launch_bounds__(256, 4) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
                                                      uint32_t seed, int mode, ouro_check *out, void **ptrs) {
+  __shared__ ouro_block_ctx<8> ctx;
+  if (STAGE) ouro_block_begin(ctx);
   payload_acc a;
   unsigned long long nulls = 0;
   const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
@@ -59,17 +63,23 @@ __global__ void __launch_bounds__(256, 4) k_round_fused(ouro_heap_dev h, const u
     const size_t i = base + (threadIdx.x & 31);
     const uint32_t sz = i < n ? sizes[i] : 0;
     unsigned char *p = nullptr;
-    if (i < n) {
+    if (STAGE) {
+      p = static_cast<unsigned char *>(stage_malloc_v<V>(ctx, h, sz, i < n));
+    } else if (i < n) {
       p = static_cast<unsigned char *>(malloc_v<V>(h, sz));
+    }
+    if (i < n) {
       if (!p) nulls++;
       if (ptrs) ptrs[i] = p;
     }
     __syncwarp();
     warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed, mode, a);
     __syncwarp();
-    if (i < n) free_v<V>(h, p);
+    if (STAGE) stage_free_v<V>(ctx, h, p);
+    else if (i < n) free_v<V>(h, p);
     __syncwarp();
   }
+  if (STAGE) ouro_block_end_v<V>(ctx, h);
   flush_acc(a, nulls, out);
 }
 
@@ -145,8 +155,13 @@ extern "C" ouro_status ouro_round_fused(ouro_heap *H, const uint32_t *d_sizes, s
   OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
   if (!n) return OURO_OK;
   const int block = 256;
-  OURO_DISPATCH(H->d.variant, (k_round_fused<V><<<grid_for(n, block, occupancy_grid(k_round_fused<V>, block)),
-                                                 block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs)));
+  if (H->d.staging) {
+    OURO_DISPATCH(H->d.variant, (k_round_fused<V, true><<<grid_for(n, block, occupancy_grid(k_round_fused<V, true>, block)),
+                                                         block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs)));
+  } else {
+    OURO_DISPATCH(H->d.variant, (k_round_fused<V, false><<<grid_for(n, block, occupancy_grid(k_round_fused<V, false>, block)),
+                                                          block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs)));
+  }
   OURO_LAUNCHED();
   return OURO_OK;
 }

@@ -10,6 +10,8 @@ namespace ouro {
 namespace detail {
 
 
+/* Staged malloc / free: page queues use the warp's shared-memory stacks;
+ * chunk queues go to the heap. */
 /* Variant-resolved malloc.  want = false: the lane asks for nothing but
  * stays in the call to help its warp carve (see page_malloc). */
 template <int V>
@@ -48,6 +50,19 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
     if (cls < 0) return;
     page_free<V>(h, cls, item, vmask);
   }
+}
+
+template <int V, int WARPS>
+__device__ __forceinline__ void *stage_malloc_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h,
+                                                unsigned long long n, bool want) {
+  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) return ouro::detail::stage_malloc<V, WARPS>(ctx, h, n, want);
+  else return malloc_v<V>(h, n, want);
+}
+
+template <int V, int WARPS>
+__device__ __forceinline__ void stage_free_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
+  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) ouro::detail::stage_free<V, WARPS>(ctx, h, p);
+  else free_v<V>(h, p);
 }
 
 /* ------------------------------------------------------------- payload */

@@ -126,8 +126,12 @@ def test_sweep_per_launch(ouro, variant, threads):
         same_canonical_as_post_create(heap.snapshot(), bytes_ // chunk)
 
 
+@pytest.mark.parametrize("staging", [False, True])
 @pytest.mark.parametrize("variant", ALL_VARIANTS)
-def test_sweep_fused_rounds(ouro, variant):
+def test_sweep_fused_rounds(ouro, variant, staging):
+    """Fused rounds, with and without shared-memory staging of freed pages
+    (page queues; chunk queues ignore the option): counts and checksums
+    exact, and every staged page is back in its queue when the kernel ends."""
     torch = torch_cuda()
     threads = 20000
     sizes = W.sweep_sizes(threads, seed=W.SEED_BASE + 12)
@@ -135,7 +139,7 @@ def test_sweep_fused_rounds(ouro, variant):
     bytes_, chunk = 256 << 20, 8192
     expect = oracle.expected_checksums(sizes, seed, 1)
     want = per_class_counts(sizes, chunk, 10)
-    with ouro.Heap(bytes_, chunk, variant) as heap:
+    with ouro.Heap(bytes_, chunk, variant, staging=staging) as heap:
         d_sizes = to_dev(sizes)
         ptrs = torch.zeros(threads, dtype=torch.int64, device="cuda")
         for r in range(3):

@@ -75,3 +75,24 @@ def test_persistent_form_is_one_launch_and_graph_replays(P):
         assert P.ouro_kernel_launches() - n1 == 20    # one fused kernel per batch
         assert run.checks() == first
         run.close()
+
+
+@pytest.mark.parametrize("variant", ["page_array", "page_vlist"])
+def test_persistent_form_with_staging(P, variant):
+    """Shared-memory staging in the persistent kernel: same per-batch checks
+    as the oracle, every page back in its queue at the end."""
+    from paper_2504_18211_gb300.batching import BatchRun
+    torch = torch_cuda()
+    sizes, offs = W.batching_workload(n_batches=16, lo=5, hi=12, seed=W.SEED_BASE + 33)
+    run = BatchRun(sizes, offs)
+    want = oracle_checks(sizes, offs, run.seed, 8192, variant)
+    with P.Heap(512 << 20, 8192, variant, staging=True) as heap:
+        for _ in range(2):
+            run.run(heap, "persistent")
+            torch.cuda.synchronize()
+            assert run.checks() == want
+        st = heap.stats()
+        assert st["error_bits"] == 0 and sum(st["live"]) == 0
+        assert sum(st["mallocs"]) == 2 * sizes.size == sum(st["frees"])
+        heap.trim()
+        same_canonical_as_post_create(heap.snapshot(), (512 << 20) // 8192)
