@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--variant", default="page_array")
+    ap.add_argument("--no-staging", action="store_true",
+                    help="headline without shared-memory staging of freed pages")
     ap.add_argument("--threads", type=int, default=THREADS)
     ap.add_argument("--heap-gib", type=int, default=HEAP_BYTES >> 30,
                     help="heap size (smaller only for profiler captures)")
@@ -67,11 +69,12 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_config(threads, variant, form="fused", heap_bytes=HEAP_BYTES):
+def workload_config(threads, variant, form="fused", heap_bytes=HEAP_BYTES, staging=True):
     return {"workload": f"size sweep: {threads} requests of 2^k B (k uniform in [4,13], seeded), "
                         f"allocate / write pattern / read back + check / free, one round per step",
             "heap_bytes": heap_bytes, "chunk_bytes": CHUNK, "threads": threads, "variant": variant,
-            "form": form, "l2": "inputs larger than L2: ~1.7 GB of payload per round (L2 129 MB)"}
+            "form": form, "staging": staging,
+            "l2": "inputs larger than L2: ~1.7 GB of payload per round (L2 129 MB)"}
 
 
 # ----------------------------------------------------------------- helpers
@@ -384,7 +387,8 @@ def main():
     ops_per_step = 2 * n
 
     heap_bytes = args.heap_gib << 30
-    heap = P.Heap(heap_bytes, CHUNK, args.variant)
+    staging = not args.no_staging
+    heap = P.Heap(heap_bytes, CHUNK, args.variant, staging=staging)
     out = torch.zeros(5, dtype=torch.int64, device="cuda")
     for _ in range(max(args.warmup, 3)):
         heap.round_fused(sizes, SEED, 1, out=out)
@@ -442,7 +446,7 @@ def main():
     achieved = alg_bytes / (mean_kernel_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
                 "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs", FALLBACK_HBM_GBS), 4),
-                "traffic": None, "kernel": "k_round_fused<page queues>",
+                "traffic": None, "kernel": "k_round_fused<page_array, staged>" if staging else "k_round_fused<page_array>",
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "bytes_model": "per request: payload written once + 37 B allocator metadata (read-back from L2)",
                 "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)"}
@@ -450,7 +454,7 @@ def main():
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_config(n, args.variant, "fused", heap_bytes), "verified": verified,
+            "config": workload_config(n, args.variant, "fused", heap_bytes, staging), "verified": verified,
             "gpu_launches": int(launches), "clocks": clk, "roofline": roofline}
 
     if not args.no_extras:
@@ -531,14 +535,15 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
                          "per_launch_ms": {k: round(x, 4) for k, x in pl2.items()}, "verified": ok}
     ex["variants"] = others
 
-    # ---- shared-memory staging of freed pages (page queues)
-    with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=True) as h3:
+    # ---- the headline round with the other staging setting
+    with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=args.no_staging) as h3:
         o3 = torch.zeros(5, dtype=torch.int64, device="cuda")
         for _ in range(3):
             h3.round_fused(sizes, SEED, 1, out=o3)
         sms = timed(torch, stream, lambda: h3.round_fused(sizes, SEED, 1, out=o3), 5)
         ok3 = P.check_to_dict(o3)["mismatches"] == 0 and h3.stats()["error_bits"] == 0
-        ex["staging"] = {"fused_mops": round(2 * n / (sms / 1e3) / 1e6, 1), "ms": round(sms, 4), "verified": ok3}
+        ex["staging_off" if not args.no_staging else "staging_on"] = {
+            "fused_mops": round(2 * n / (sms / 1e3) / 1e6, 1), "ms": round(sms, 4), "verified": ok3}
 
     # ---- malloc latency histogram (warm heap, malloc-only batch)
     hist = torch.zeros(256, dtype=torch.int64, device="cuda")
