@@ -69,6 +69,29 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of the size batch replica `rank` draws: every replica runs the
+    same workload shape on its own heap with its own requests."""
+    from paper_2504_18211_gb300 import workloads as W
+    return W.SEED_BASE + 1 + rank
+
+
+def max_over_ranks(dist, ms: float, device) -> float:
+    """The slowest replica's timed region (ms); `dist` None for one process."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ws: int, steps: int, ops_per_step: int, total_ms: float) -> float:
+    """Operations of all replicas over the slowest replica's time, in Mops/s
+    (weak scaling: each replica does ops_per_step per step)."""
+    return ws * steps * ops_per_step / (total_ms / 1e3) / 1e6
+
+
 def workload_config(threads, variant, form="fused", heap_bytes=HEAP_BYTES, staging=True):
     return {"workload": f"size sweep: {threads} requests of 2^k B (k uniform in [4,13], seeded), "
                         f"allocate / write pattern / read back + check / free, one round per step",
@@ -381,7 +404,7 @@ def main():
     P.load()
 
     n = args.threads
-    sizes_np = W.sweep_sizes(n, seed=W.SEED_BASE + 1 + rank)      # each replica its own batch
+    sizes_np = W.sweep_sizes(n, seed=replica_seed(rank))          # each replica its own batch
     sizes = torch.from_numpy(sizes_np.view(np.int32)).cuda()
     stream = torch.cuda.current_stream()
     ops_per_step = 2 * n
@@ -415,11 +438,8 @@ def main():
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps * ops_per_step / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
+    value = whole_job_value(ws, args.steps, ops_per_step, total_ms)
     chk = P.check_to_dict(out)
     st = heap.stats()
 
