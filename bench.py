@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--heap-gib", type=int, default=HEAP_BYTES >> 30,
                     help="heap size (smaller only for profiler captures)")
     ap.add_argument("--no-extras", action="store_true", help="headline only (used under a profiler)")
+    ap.add_argument("--form", choices=("fused", "per_launch"), default="fused",
+                    help="fused: one kernel per round; per_launch: malloc / write / check / free kernels")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--workload", choices=("sweep", "batching", "serving", "graph"), default="sweep",
                     help="sweep: the headline size sweep; batching: 256 uneven batches, every form + autotuner; "
@@ -67,6 +69,31 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fused
+# launch of the default workload, from one ncu capture of the kernel built
+# from the sources whose digest is recorded; null once they change.
+FUSED_KERNEL_SOURCES = ("include/ouro_device.cuh", "paper_2504_18211_gb300/csrc/ouro_payload.cuh",
+                        "paper_2504_18211_gb300/csrc/ouro_kernels.cu", "paper_2504_18211_gb300/csrc/ouro_internal.cuh")
+FUSED_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+
+
+def kernel_sources_digest() -> str:
+    import hashlib
+    d = hashlib.sha256()
+    for rel in FUSED_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            d.update(f.read())
+    return d.hexdigest()
+
+
+def recorded_traffic(args, staging, n, heap_bytes):
+    default = (args.form == "fused" and args.variant == "page_array" and staging and n == THREADS
+               and heap_bytes == HEAP_BYTES)
+    if not default or FUSED_TRAFFIC["bytes_per_launch"] is None:
+        return None
+    return FUSED_TRAFFIC["bytes_per_launch"] if kernel_sources_digest() == FUSED_TRAFFIC["sources_sha256"] else None
 
 
 def replica_seed(rank: int) -> int:
@@ -413,8 +440,19 @@ def main():
     staging = not args.no_staging
     heap = P.Heap(heap_bytes, CHUNK, args.variant, staging=staging)
     out = torch.zeros(5, dtype=torch.int64, device="cuda")
+    if args.form == "fused":
+        def step():
+            heap.round_fused(sizes, SEED, 1, out=out)
+    else:
+        ptrs = torch.empty(n, dtype=torch.int64, device="cuda")
+
+        def step():
+            heap.malloc(sizes, ptrs)
+            P.pattern_write(ptrs, sizes, SEED, 1)
+            P.pattern_check(ptrs, sizes, SEED, 1, out)
+            heap.free(ptrs)
     for _ in range(max(args.warmup, 3)):
-        heap.round_fused(sizes, SEED, 1, out=out)
+        step()
     torch.cuda.synchronize()
 
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
@@ -428,7 +466,7 @@ def main():
     t_start.record(stream)
     for k in range(args.steps):
         ev[2 * k].record(stream)
-        heap.round_fused(sizes, SEED, 1, out=out)
+        step()
         ev[2 * k + 1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -461,20 +499,28 @@ def main():
     # each block follows the block's write within the same warp and is served
     # by L2 (ncu: DRAM reads ~1-2 % of DRAM writes), so HBM bytes per request
     # are payload + metadata
-    alg_bytes = payload + meta_per_req * n
+    if args.form == "fused":
+        alg_bytes = payload + meta_per_req * n
+        kernel = f"k_round_fused<{args.variant}{', staged' if staging else ''}>"
+        model = "per request: payload written once + 37 B allocator metadata (read-back from L2)"
+    else:
+        # four kernels: the check reads the payload back from HBM; malloc
+        # 28 B, free 25 B, write and check 12 B each of pointer and size
+        alg_bytes = 2 * payload + 77 * n
+        kernel = "per-launch round (malloc, write, check, free)"
+        model = "per request: payload written and read back + 77 B of allocator and kernel metadata"
     mean_kernel_ms = statistics.mean(step_ms)
     achieved = alg_bytes / (mean_kernel_ms / 1e3) / 1e9
+    traffic = recorded_traffic(args, staging, n, heap_bytes)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
                 "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs", FALLBACK_HBM_GBS), 4),
-                "traffic": None, "kernel": "k_round_fused<page_array, staged>" if staging else "k_round_fused<page_array>",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "bytes_model": "per request: payload written once + 37 B allocator metadata (read-back from L2)",
-                "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)"}
+                "traffic": traffic, "kernel": kernel, "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_model": model, "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)"}
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": workload_config(n, args.variant, "fused", heap_bytes, staging), "verified": verified,
+            "config": workload_config(n, args.variant, args.form, heap_bytes, staging), "verified": verified,
             "gpu_launches": int(launches), "clocks": clk, "roofline": roofline}
 
     if not args.no_extras:
