@@ -23,9 +23,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ouro_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-PAGE_ARRAY, CHUNK_ARRAY, PAGE_VLIST, CHUNK_VLIST = 0, 1, 2, 3
+PAGE_ARRAY, CHUNK_ARRAY, PAGE_VLIST, CHUNK_VLIST, PAGE_VARRAY, CHUNK_VARRAY = 0, 1, 2, 3, 4, 5
 VARIANTS = {"page_array": PAGE_ARRAY, "chunk_array": CHUNK_ARRAY,
-            "page_vlist": PAGE_VLIST, "chunk_vlist": CHUNK_VLIST}
+            "page_vlist": PAGE_VLIST, "chunk_vlist": CHUNK_VLIST,
+            "page_varray": PAGE_VARRAY, "chunk_varray": CHUNK_VARRAY}
 MAX_CLASSES = 17
 ERR_BAD_FREE, ERR_DOUBLE_FREE, ERR_QUEUE_FULL = 1, 2, 4
 

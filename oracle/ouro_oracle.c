@@ -69,10 +69,15 @@ struct orc_heap {
 static int is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
 static int log2u(uint64_t x) { int l = 0; while ((1ull << l) < x) l++; return l; }
 static int page_variant(const orc_heap *h) {
-  return h->variant == ORC_PAGE_ARRAY || h->variant == ORC_PAGE_VLIST;
+  return h->variant == ORC_PAGE_ARRAY || h->variant == ORC_PAGE_VLIST || h->variant == ORC_PAGE_VARRAY;
 }
-static int vlist(const orc_heap *h) {
-  return h->variant == ORC_PAGE_VLIST || h->variant == ORC_CHUNK_VLIST;
+/* virtualized queues, list or array form: storage in segments of the heap */
+static int virt(const orc_heap *h) {
+  return h->variant == ORC_PAGE_VLIST || h->variant == ORC_CHUNK_VLIST ||
+         h->variant == ORC_PAGE_VARRAY || h->variant == ORC_CHUNK_VARRAY;
+}
+static int varray(const orc_heap *h) {
+  return h->variant == ORC_PAGE_VARRAY || h->variant == ORC_CHUNK_VARRAY;
 }
 
 /* Classes are the powers of two from 16 B up to the chunk size
@@ -107,7 +112,7 @@ static int live_get(const orc_heap *h, uint64_t off) {
 orc_heap *orc_create(uint64_t bytes, uint64_t chunk_bytes, int variant, uint64_t queue_cap) {
   if (!is_pow2(chunk_bytes) || chunk_bytes < 256 || chunk_bytes > (1u << 20)) return NULL;
   if (bytes == 0 || bytes % chunk_bytes) return NULL;
-  if (variant < ORC_PAGE_ARRAY || variant > ORC_CHUNK_VLIST) return NULL;
+  if (variant < ORC_PAGE_ARRAY || variant > ORC_CHUNK_VARRAY) return NULL;
   orc_heap *h = (orc_heap *)calloc(1, sizeof(orc_heap));
   if (!h) return NULL;
   h->bytes = bytes;
@@ -186,16 +191,20 @@ static int seg_ensure(orc_heap *h, int c, uint64_t pos) {
   }
   return 0;
 }
-/* A segment retires once all its positions were consumed and a successor exists. */
+/* A segment retires once all its positions were consumed.  The list form
+ * also needs a successor, because the list is entered through its oldest
+ * segment; the array form finds every segment through its index, so its
+ * last segment retires too. */
 static void seg_retire(orc_heap *h, int c) {
-  while (h->segs[c].n >= 2 && h->qhead[c] >= (h->seg_first[c] + 1) * h->seg_cap) {
+  const uint64_t keep = varray(h) ? 1 : 2;
+  while (h->segs[c].n >= keep && h->qhead[c] >= (h->seg_first[c] + 1) * h->seg_cap) {
     fifo_push(&h->spare[c], fifo_pop_front(&h->segs[c]));
     h->seg_first[c]++;
   }
 }
 
 static int q_push(orc_heap *h, int c, uint64_t item) {
-  if (vlist(h)) {
+  if (virt(h)) {
     if (seg_ensure(h, c, h->qtail[c])) { h->err |= ORC_ERR_QUEUE_FULL; return -1; }
     h->qtail[c]++;
     seg_retire(h, c);
@@ -204,7 +213,7 @@ static int q_push(orc_heap *h, int c, uint64_t item) {
   return 0;
 }
 static uint64_t q_pop(orc_heap *h, int c) {
-  if (vlist(h)) { h->qhead[c]++; seg_retire(h, c); }
+  if (virt(h)) { h->qhead[c]++; seg_retire(h, c); }
   return fifo_pop_front(&h->q[c]);
 }
 
@@ -220,7 +229,7 @@ static int carve(orc_heap *h, int c) {
     if (qc > h->queue_cap) qc = h->queue_cap;
     if ((h->carved_now[c] + 1) * ppc > qc) return -1;
   }
-  if (vlist(h)) {
+  if (virt(h)) {
     /* queue storage first: segments for every position the carve will fill */
     uint64_t need = page_variant(h) ? ppc : 1;
     if (seg_ensure(h, c, h->qtail[c] + need - 1)) return -1;
@@ -355,7 +364,7 @@ void orc_trim(orc_heap *h) {
   for (uint64_t i = 0; i < np; i++) fifo_push(&h->pool, pv[i]);
   free(pv);
   /* 5. virtualized queues are re-laid from position 0, class by class */
-  if (vlist(h)) {
+  if (virt(h)) {
     for (int c = 0; c < h->n_classes; c++) {
       fifo items = h->q[c];
       memset(&h->q[c], 0, sizeof(fifo));

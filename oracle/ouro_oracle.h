@@ -34,7 +34,12 @@ extern "C" {
 
 #define ORC_MAX_CLASSES 17          /* 16 B .. 1 MiB */
 
-enum { ORC_PAGE_ARRAY = 0, ORC_CHUNK_ARRAY = 1, ORC_PAGE_VLIST = 2, ORC_CHUNK_VLIST = 3 };
+/* queue forms (Sec. 3 lists six: page / chunk queues, each as a plain
+ * array, a virtualized array and a virtualized list) */
+enum {
+  ORC_PAGE_ARRAY = 0, ORC_CHUNK_ARRAY = 1, ORC_PAGE_VLIST = 2, ORC_CHUNK_VLIST = 3,
+  ORC_PAGE_VARRAY = 4, ORC_CHUNK_VARRAY = 5
+};
 
 /* error bits (sticky) */
 enum {

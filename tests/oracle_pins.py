@@ -27,7 +27,12 @@ import oracle
 from setmodel import SetModel, ceil_log2
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-ALL_VARIANTS = ("page_array", "chunk_array", "page_vlist", "chunk_vlist")
+ALL_VARIANTS = ("page_array", "chunk_array", "page_vlist", "chunk_vlist", "page_varray", "chunk_varray")
+
+
+def plain_array(variant):
+    """Plain array queues hold their storage outside the heap."""
+    return variant in ("page_array", "chunk_array")
 
 
 def heap(lib_path, bytes_, chunk, variant, cap=0):
@@ -67,7 +72,7 @@ def pin_layout(lib_path):
                     offs.append(o)
                     assert len(offs) <= bytes_ // page
                 st = h.stats()
-                if variant.endswith("array"):
+                if plain_array(variant):
                     assert sorted(offs) == list(range(0, bytes_, page)), (variant, chunk, c)
                 else:
                     # queue segments take whole chunks out of the same heap
@@ -157,7 +162,7 @@ def pin_brute_force(lib_path, max_len=4, random_runs=60, random_len=250):
                 _run_sequence(lib_path, variant, 2 * 256, 256, ops)
     rng = np.random.default_rng(20250424)
     for variant in ALL_VARIANTS:
-        nulls = variant.endswith("array")
+        nulls = plain_array(variant)
         for _ in range(random_runs):
             ops = []
             for _ in range(random_len):
@@ -235,18 +240,37 @@ def pin_restore(lib_path):
 
 def pin_segments(lib_path):
     """Virtualized queue storage (Sec. 4.3) under the stated rule: a segment is
-    one chunk holding (chunk - 64) / 8 cells, and it retires only once every
-    position in it was consumed and a successor exists.  Closed form with
-    512 B chunks (56 cells) and 64 B requests (8 pages per chunk): 56 requests
-    use 7 data chunks and exactly fill segment 0; the 57th needs segment 1."""
-    h = heap(lib_path, 64 * 512, 512, "page_vlist")
-    for _ in range(56):
+    one chunk holding (chunk - 64) / 8 cells, and it retires once every
+    position in it was consumed -- in the list form only when a successor
+    exists too.  Closed form with 512 B chunks (56 cells) and 64 B requests
+    (8 pages per chunk): 56 requests use 7 data chunks and exactly fill
+    segment 0; the 57th needs segment 1.
+      list:  segment 0 stays (no successor) -> (1 live, 0 spare, bump 8);
+             the 57th links segment 1 (chunk 8), carves chunk 9, then
+             segment 0 retires -> (1, 1, 10).
+      array: segment 0 retires with its last consumer -> (0, 1, 8); the 57th
+             reuses it as segment 1 and carves chunk 8 -> (1, 0, 9)."""
+    for variant, after56, after57 in (("page_vlist", (1, 0, 8), (1, 1, 10)),
+                                      ("page_varray", (0, 1, 8), (1, 0, 9))):
+        h = heap(lib_path, 64 * 512, 512, variant)
+        for _ in range(55):
+            assert h.malloc(64) >= 0
+        st = h.stats()      # one position of segment 0 is still unconsumed: it stays
+        assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == (1, 0, 8), (variant, st)
         assert h.malloc(64) >= 0
-    st = h.stats()
-    assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == (1, 0, 8), st
-    assert h.malloc(64) >= 0
-    st = h.stats()
-    assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == (1, 1, 10), st
+        st = h.stats()
+        assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == after56, (variant, st)
+        assert h.malloc(64) >= 0
+        st = h.stats()
+        assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == after57, (variant, st)
+    # chunk queues hold one position per carved chunk: 56 chunks of one class
+    # fill segment 0 exactly (heap of 64 chunks of 512 B, requests of 512 B)
+    for variant, after56 in (("chunk_vlist", (1, 0, 57)), ("chunk_varray", (0, 1, 57))):
+        h = heap(lib_path, 64 * 512, 512, variant)
+        for _ in range(56):
+            assert h.malloc(512) >= 0
+        st = h.stats()
+        assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == after56, (variant, st)
 
 
 def pin_fmix32(lib_path):

@@ -30,7 +30,10 @@ MUTANTS = {
     "no_double_free_check": ("if (!live_get(h, off))", "if (0)"),
     "bump_past_end": ("if (h->bump < h->n_chunks) return", "if (h->bump <= h->n_chunks) return"),
     "page_array_cap_ignored": ("if ((h->carved_now[c] + 1) * ppc > qc) return -1;", ""),
-    "segment_retired_early": ("while (h->segs[c].n >= 2 && h->qhead[c]", "while (h->segs[c].n >= 1 && h->qhead[c]"),
+    "segment_retired_early": ("const uint64_t keep = varray(h) ? 1 : 2;", "const uint64_t keep = 1;"),
+    "varray_waits_for_successor": ("const uint64_t keep = varray(h) ? 1 : 2;", "const uint64_t keep = 2;"),
+    "segment_retired_unconsumed": ("h->qhead[c] >= (h->seg_first[c] + 1) * h->seg_cap",
+                                   "h->qhead[c] + 1 >= (h->seg_first[c] + 1) * h->seg_cap"),
     "trim_reclaims_partial": ("if (fr == ppc) reclaim[x] = 1;", "if (fr + 1 >= ppc) reclaim[x] = 1;"),
     "chunk_full_not_popped": ("if (h->free_pages[x] == 0) q_pop(h, c);", ""),
     "fmix_shift": ("x ^= x >> 13;", "x ^= x >> 12;"),
