@@ -76,7 +76,8 @@ def dist_env():
 # from the sources whose digest is recorded; null once they change.
 FUSED_KERNEL_SOURCES = ("include/ouro_device.cuh", "paper_2504_18211_gb300/csrc/ouro_payload.cuh",
                         "paper_2504_18211_gb300/csrc/ouro_kernels.cu", "paper_2504_18211_gb300/csrc/ouro_internal.cuh")
-FUSED_TRAFFIC = {"sources_sha256": None, "bytes_per_launch": None}
+FUSED_TRAFFIC = {"sources_sha256": "064c9761870b3d143e29ee556293acb3e20cf9d1332a9f1839f1aca34fff759a",
+                 "bytes_per_launch": 1627118080}
 
 
 def kernel_sources_digest() -> str:
