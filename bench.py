@@ -587,7 +587,7 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
 
     # ---- the other page-queue variant
     others = {}
-    for v in ("page_array", "page_vlist", "chunk_array", "chunk_vlist"):
+    for v in ("page_array", "page_vlist", "chunk_array", "chunk_vlist", "page_varray", "chunk_varray"):
         if v == args.variant:
             continue
         with P.Heap(HEAP_BYTES, CHUNK, v) as h2:

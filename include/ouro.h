@@ -43,12 +43,27 @@ enum {
   OURO_ENOTSUP = 5    /* the heap's variant does not offer this operation */
 };
 
-/* queue variants: page or chunk queues (Sec. 4.1, 4.2), array or virtualized list (Sec. 4.3) */
+/* queue variants (the six of Sec. 3): page or chunk queues (Sec. 4.1, 4.2),
+ * each as a plain array, a virtualized list or a virtualized array (Sec. 4.3).
+ *   plain array:        a ring of slots outside the heap, per class
+ *                       next_pow2(min(bytes/page, array_queue_capacity) + 2^19)
+ *                       slots of 8 B;
+ *   virtualized list:   slots live in heap chunks (segments) linked in
+ *                       position order, found by a walk (with a lookaside);
+ *   virtualized array:  slots live in heap chunks found by index through a
+ *                       per-class directory of 8-B entries, next_pow2 of
+ *                       ceil((bytes/page + 2^20) / segment slots) + 4
+ *                       entries (chunk queues: n_chunks in place of
+ *                       bytes/page).  A segment returns to its class's spare
+ *                       stack once all its positions are produced and
+ *                       consumed. */
 typedef enum {
   OURO_PAGE_ARRAY = 0,
   OURO_CHUNK_ARRAY = 1,
   OURO_PAGE_VLIST = 2,
-  OURO_CHUNK_VLIST = 3
+  OURO_CHUNK_VLIST = 3,
+  OURO_PAGE_VARRAY = 4,
+  OURO_CHUNK_VARRAY = 5
 } ouro_variant;
 
 /* device error bits (sticky until ouro_heap_reset) */

@@ -48,6 +48,19 @@
 #define OURO_SHARDS 32
 #define OURO_SEG_HDR 64
 
+/* queue storage forms */
+#define OURO_QF_RING 0     /* plain array: a ring of slots outside the heap */
+#define OURO_QF_LIST 1     /* virtualized list: segments linked in position order */
+#define OURO_QF_VARRAY 2   /* virtualized array: segments found through a directory */
+__host__ __device__ constexpr int ouro_qform(int v) {
+  return (v == OURO_PAGE_VLIST || v == OURO_CHUNK_VLIST)     ? OURO_QF_LIST
+         : (v == OURO_PAGE_VARRAY || v == OURO_CHUNK_VARRAY) ? OURO_QF_VARRAY
+                                                            : OURO_QF_RING;
+}
+__host__ __device__ constexpr bool ouro_page_queues(int v) {
+  return v == OURO_PAGE_ARRAY || v == OURO_PAGE_VLIST || v == OURO_PAGE_VARRAY;
+}
+
 enum {
   OURO_ST_MALLOC = 0, OURO_ST_FREE = 1, OURO_ST_FAILED = 2, OURO_ST_CARVE = 3,
   OURO_ST_REPUSH = 4, OURO_ST_CANCEL = 5, OURO_ST_DEAD = 6, OURO_ST_SEG = 7
@@ -160,7 +173,7 @@ enum {
   OURO_SITE_SPARE = 1, OURO_SITE_VL_FIRST, OURO_SITE_VL_NEXT, OURO_SITE_VL_WALK, OURO_SITE_PUT,
   OURO_SITE_PUSH_ONE, OURO_SITE_PAGE_GIVEUP, OURO_SITE_PAGE_CHECKED, OURO_SITE_CLAIM,
   OURO_SITE_CHUNK_GIVEUP, OURO_SITE_CHUNK_DOUBLE, OURO_SITE_BAD_FREE, OURO_SITE_PAGE_DOUBLE,
-  OURO_SITE_TRIM, OURO_SITE_GRAPH_LOCK
+  OURO_SITE_TRIM, OURO_SITE_GRAPH_LOCK, OURO_SITE_VA_NEW, OURO_SITE_VA_WAIT
 };
 __device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits, unsigned site) {
   atomicOr(&gl(h)->error_bits, bits);
@@ -320,22 +333,82 @@ __device__ inline void vl_advance(const ouro_heap_dev &h, int c) {
   }
 }
 
+/* ------------------------------------------ virtualized-array directory */
+/* Entry of segment index s in the directory of class c: (index << 32) |
+ * chunk, with chunk OURO_NIL while segment s does not exist yet and
+ * OURO_BUSY while its one creator sets it up.  The directory has D = 2^k
+ * entries; segment s uses entry s mod D, whose index field runs ahead by D
+ * each time a segment in it retires. */
+__device__ __forceinline__ unsigned long long *va_entry(const ouro_heap_dev &h, int c, unsigned long long s) {
+  return h.cells + h.ring_off[c] + (s & h.ring_mask[c]);
+}
+
+/* Segment x has seen all its position events: its entry is emptied for the
+ * next lap (index + D) and the chunk joins the class spare stack. */
+__device__ inline void va_retire(const ouro_heap_dev &h, int c, unsigned x) {
+  const unsigned idx = hi32(ld_acq(&seg_of(h, x)->link));
+  st_rel(va_entry(h, c, idx), pack(idx + (unsigned)(h.ring_mask[c] + 1), OURO_NIL));
+  spare_push(h, c, x);
+}
+
+/* Slot of position pos in the virtualized array of class c.  create: make
+ * the segment if it does not exist (one creator, the others wait);
+ * otherwise null while it does not exist.  Null too for a segment that has
+ * retired already (only a look-ahead can ask for one: a thread holding an
+ * unfinished position keeps its segment alive). */
+__device__ inline unsigned long long *va_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                              bool create) {
+  const unsigned long long s = pos / h.seg_cap;
+  const unsigned s32 = (unsigned)s;
+  const unsigned off = (unsigned)(pos - s * h.seg_cap);
+  unsigned long long *e = va_entry(h, c, s);
+  unsigned ns = h.backoff_min_ns;
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    const unsigned long long v = ld_acq(e);
+    const int d = (int)(hi32(v) - s32);
+    const unsigned x = lo32(v);
+    if (d > 0) return nullptr;
+    if (d == 0 && x < OURO_BUSY) return seg_cells(h, x) + off;
+    if (!create) return nullptr;
+    if (d == 0 && x == OURO_NIL) {
+      if (cas_ar(e, v, pack(s32, OURO_BUSY)) == v) {
+        const unsigned nx = seg_new(h, c, s32);
+        if (nx == OURO_NIL) {
+          st_rel(e, v);
+          set_error(h, OURO_ERR_QUEUE_FULL, OURO_SITE_VA_NEW);
+          return nullptr;
+        }
+        st_rel(e, pack(s32, nx));
+        return seg_cells(h, nx) + off;
+      }
+      continue;
+    }
+    /* being created, or the entry still serves segment s - D (wait for it to retire) */
+    __nanosleep(ns);
+    ns = min(ns * 2, h.backoff_max_ns);
+  }
+  set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_VA_WAIT);
+  return nullptr;
+}
+
 /* n position events on the segment holding `cell` */
-__device__ inline void vl_event(const ouro_heap_dev &h, int c, const unsigned long long *cell,
-                                unsigned n) {
+template <int QF>
+__device__ inline void seg_event(const ouro_heap_dev &h, int c, const unsigned long long *cell, unsigned n) {
   unsigned x = (unsigned)(((const unsigned char *)cell - h.base) >> h.log2_chunk);
   unsigned r = atomicAdd(&seg_of(h, x)->done, n) + n;
   if (r == 2u * h.seg_cap) {
     __threadfence();
-    vl_advance(h, c);
+    if (QF == OURO_QF_LIST) vl_advance(h, c);
+    else va_retire(h, c, x);
   }
 }
 
 /* Position events of the lanes of mask (every lane of mask calls): lanes
  * with `active` and a slot count one event on the segment of their slot;
  * lanes on the same segment are summed into one atomic. */
-__device__ inline void vl_event_warp(const ouro_heap_dev &h, int c, const unsigned long long *cell, bool active,
-                                     unsigned mask) {
+template <int QF>
+__device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsigned long long *cell, bool active,
+                                      unsigned mask) {
   const bool on = active && cell;
   const unsigned x = on ? (unsigned)(((const unsigned char *)cell - h.base) >> h.log2_chunk) : OURO_NIL;
   const unsigned g = __match_any_sync(mask, x) & __ballot_sync(mask, on);
@@ -344,7 +417,8 @@ __device__ inline void vl_event_warp(const ouro_heap_dev &h, int c, const unsign
     const unsigned r = atomicAdd(&seg_of(h, x)->done, n) + n;
     if (r == 2u * h.seg_cap) {
       __threadfence();
-      vl_advance(h, c);
+      if (QF == OURO_QF_LIST) vl_advance(h, c);
+      else va_retire(h, c, x);
     }
   }
 }
@@ -431,12 +505,33 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
   return nullptr;
 }
 
-/* slot of position pos for variant V (template-resolved) */
-template <bool VL>
+/* slot of position pos for storage form QF (template-resolved) */
+template <int QF>
 __device__ __forceinline__ unsigned long long *slot_at(const ouro_heap_dev &h, int c,
                                                        unsigned long long pos, bool create) {
-  if (VL) return vl_slot(h, c, pos, create);
+  if (QF == OURO_QF_LIST) return vl_slot(h, c, pos, create);
+  if (QF == OURO_QF_VARRAY) return va_slot(h, c, pos, create);
   return ring_slot(h, c, pos);
+}
+
+/* slot of position pos, storage form chosen at run time (host-side kernels) */
+__device__ inline unsigned long long *slot_any(const ouro_heap_dev &h, int c, unsigned long long pos) {
+  switch (ouro_qform((int)h.variant)) {
+    case OURO_QF_LIST: return vl_slot(h, c, pos, false);
+    case OURO_QF_VARRAY: return va_slot(h, c, pos, false);
+    default: return ring_slot(h, c, pos);
+  }
+}
+
+/* Queue storage first: make sure the segments for positions [first, last]
+ * exist before a carve takes data chunks (virtualized forms). */
+template <int QF>
+__device__ inline void seg_prepare(const ouro_heap_dev &h, int c, unsigned long long first,
+                                   unsigned long long last) {
+  if (QF == OURO_QF_LIST) vl_slot(h, c, last, true);
+  if (QF == OURO_QF_VARRAY)
+    for (unsigned long long s = first / h.seg_cap; s <= last / h.seg_cap; ++s)
+      va_slot(h, c, s * h.seg_cap, true);
 }
 
 /* ------------------------------------------------------- slot operations */
@@ -499,15 +594,16 @@ __device__ inline int give_up(const ouro_heap_dev &h, int c, unsigned long long 
 }
 
 /* Queue one item at a fresh producer position (re-queue after a give-up). */
-template <bool VL>
+template <int QF>
 __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
+  constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, c);
   for (int tries = 0; tries < 64; ++tries) {
     unsigned long long t = atomicAdd(&q->tail.v, 1ull);
-    unsigned long long *cell = slot_at<VL>(h, c, t, true);
+    unsigned long long *cell = slot_at<QF>(h, c, t, true);
     if (!cell) return;   /* error already recorded */
     int rc = put_at(h, cell, t, item, false, VL);
-    if (VL) vl_event(h, c, cell, 1);
+    if (VL) seg_event<QF>(h, c, cell, 1);
     if (rc == 0) return;
     if (rc < 0) return;
     stat_add(h, c, OURO_ST_REPUSH, 1);
@@ -523,7 +619,8 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
  * get the null marker. */
 template <int V>
 __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
-  constexpr bool VL = (V == OURO_PAGE_VLIST);
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
   const unsigned ppc_log = h.log2_chunk - 4 - c;
@@ -545,7 +642,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
         /* queue storage first: segments for every slot this carve (or its
          * null answers) will write, before the data chunks are taken */
         unsigned long long last = max(hd, t + (ask << ppc_log)) - 1;
-        vl_slot(h, c, last, true);
+        seg_prepare<QF>(h, c, t, last);
       }
       if (ask) r = take_chunks(h, (unsigned)ask);
       m = r.k1 + r.k2;
@@ -592,7 +689,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
         if (i < total) {
           const unsigned x = range_chunk(h, r, (unsigned)(i >> ppc_log));
           item[f] = (x << ppc_log) | (unsigned)(i & (ppc - 1));
-          cell[f] = slot_at<VL>(h, c, t0 + i, true);      /* null: queue storage exhausted (recorded) */
+          cell[f] = slot_at<QF>(h, c, t0 + i, true);      /* null: queue storage exhausted (recorded) */
         }
       }
 #pragma unroll
@@ -606,8 +703,8 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
         const unsigned long long p = t0 + i;
         int rc = 0;
         if (cell[f] && got[f] != slot(p, 0)) rc = put_at(h, cell[f], p, item[f], false, VL);
-        if (VL) vl_event_warp(h, c, cell[f], i < total, vmask);
-        if (cell[f] && rc == 1) push_one<VL>(h, c, item[f]);
+        if (VL) seg_event_warp<QF>(h, c, cell[f], i < total, vmask);
+        if (cell[f] && rc == 1) push_one<QF>(h, c, item[f]);
       }
     }
   }
@@ -626,9 +723,9 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
     for (unsigned long long i0 = 0; i0 < dn; i0 += nl) {
       const unsigned long long i = i0 + rk;
       const bool act = i < dn;
-      unsigned long long *cell = act ? slot_at<VL>(h, c, dt + i, true) : nullptr;
+      unsigned long long *cell = act ? slot_at<QF>(h, c, dt + i, true) : nullptr;
       if (cell) put_at(h, cell, dt + i, 0, true, VL);
-      if (VL) vl_event_warp(h, c, cell, act, vmask);
+      if (VL) seg_event_warp<QF>(h, c, cell, act, vmask);
     }
   }
   __syncwarp(vmask);
@@ -642,7 +739,8 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
  * lane allocates still fills new slots 32 lanes wide. */
 template <int V>
 __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
-  constexpr bool VL = (V == OURO_PAGE_VLIST);
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
   const bool req = cls >= 0;
   ouro_qhdr *q = qh(h, req ? cls : 0);
   const unsigned lane = laneid();
@@ -658,10 +756,10 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   int st = req ? 0 : 3;   /* 0 waiting, 1 item, 2 null answer, 3 gave up (helpers: nothing asked) */
   unsigned long long *cell = nullptr;
   if (VL) {   /* the leader finds its segment; lanes in the same segment reuse it */
-    unsigned long long *c0 = (req && lane == leader) ? vl_slot(h, cls, p0, false) : nullptr;
+    unsigned long long *c0 = (req && lane == leader) ? slot_at<QF>(h, cls, p0, false) : nullptr;
     c0 = reinterpret_cast<unsigned long long *>(
         __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
-    if (req) cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + rank : vl_slot(h, cls, pos, false);
+    if (req) cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + rank : slot_at<QF>(h, cls, pos, false);
   } else if (req) {
     cell = ring_slot(h, cls, pos);
   }
@@ -673,7 +771,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
     for (unsigned it = 0;; ++it) {
       bool debt = false, progressed = false;
       if (st == 0) {
-        if (VL && !cell) cell = vl_slot(h, cls, pos, false);
+        if (VL && !cell) cell = slot_at<QF>(h, cls, pos, false);
         if (cell) st = try_take<VL>(h, cls, cell, pos, &item);
         if (st) progressed = true;
         else debt = pos >= ld_acq(&q->tail.v);
@@ -694,7 +792,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       if (!waiting) break;
       if (it >= h.spin_limit) {
         if (st == 0) {   /* give the position up so its producer re-queues the item */
-          if (!cell) cell = slot_at<VL>(h, cls, pos, true);
+          if (!cell) cell = slot_at<QF>(h, cls, pos, true);
           int g = cell ? give_up<VL>(h, cls, cell, pos, &item) : 0;
           st = g ? g : 3;
           gave_up = g == 3;
@@ -713,7 +811,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       }
     }
   }
-  if (VL) vl_event_warp(h, cls, cell, st != 0 && (st != 3 || gave_up), vmask);
+  if (VL) seg_event_warp<QF>(h, cls, cell, st != 0 && (st != 3 || gave_up), vmask);
 
   void *res = nullptr;
   if (st == 1) {
@@ -738,7 +836,8 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
 
 template <int V>
 __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsigned vmask) {
-  constexpr bool VL = (V == OURO_PAGE_VLIST);
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, cls);
   const unsigned lane = laneid();
   const unsigned grp = __match_any_sync(vmask, cls);
@@ -753,18 +852,18 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
   t = t0 + rank;
   unsigned long long *cell;
   if (VL) {   /* the leader finds (or links) its segment; lanes in the same segment reuse it */
-    unsigned long long *c0 = lane == leader ? vl_slot(h, cls, t0, true) : nullptr;
+    unsigned long long *c0 = lane == leader ? slot_at<QF>(h, cls, t0, true) : nullptr;
     c0 = reinterpret_cast<unsigned long long *>(
         __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
-    cell = (c0 && t / h.seg_cap == t0 / h.seg_cap) ? c0 + rank : vl_slot(h, cls, t, true);
+    cell = (c0 && t / h.seg_cap == t0 / h.seg_cap) ? c0 + rank : slot_at<QF>(h, cls, t, true);
   } else {
     cell = ring_slot(h, cls, t);
   }
   int rc = cell ? put_at(h, cell, t, item, false, VL) : 0;   /* no slot: queue storage exhausted, page lost (recorded) */
-  if (VL) vl_event_warp(h, cls, cell, true, vmask);
+  if (VL) seg_event_warp<QF>(h, cls, cell, true, vmask);
   if (rc == 1) {
     stat_add(h, cls, OURO_ST_REPUSH, 1);
-    push_one<VL>(h, cls, item);
+    push_one<QF>(h, cls, item);
   }
 }
 
@@ -798,15 +897,16 @@ __device__ __forceinline__ int locate(const ouro_heap_dev &h, const void *p, uns
 #define OURO_CQ_ID(it) ((it) & ((1u << 26) - 1))
 #define OURO_CQ_CNT(it) ((((it) >> 26) & 31u) + 1)
 
-template <bool VL>
+template <int QF>
 __device__ inline void chunk_push(const ouro_heap_dev &h, int c, unsigned x) {
-  push_one<VL>(h, c, x);
+  push_one<QF>(h, c, x);
 }
 
 /* Called by every lane of vmask; lane `owner` holds the carve lock of class c. */
 template <int V>
 __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
-  constexpr bool VL = (V == OURO_CHUNK_VLIST);
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
   const unsigned ppc_log = h.log2_chunk - 4 - c;
@@ -824,7 +924,7 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
         hd = ld_acq(&q->head.v);
         if (hd <= t) break;
         unsigned d = (unsigned)min(hd - t, 8ull * nl);   /* each lane plans up to 8 positions */
-        if (VL) vl_slot(h, c, t + d - 1, true);           /* segments before chunks */
+        seg_prepare<QF>(h, c, t, t + d - 1);              /* segments before chunks */
         if (atomicCAS(&q->tail.v, t, t + d) == t) { D = d; break; }
       }
     }
@@ -841,7 +941,7 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
       need[r] = 0;
       cell[r] = nullptr;
       if (i < D) {
-        cell[r] = slot_at<VL>(h, c, t + i, true);
+        cell[r] = slot_at<QF>(h, c, t + i, true);
         unsigned long long v = cell[r] ? ld_acq(cell[r]) : 0;
         unsigned posted = (cell[r] && slot_d(v, t + i) == 0) ? lo32(v) : 0;
         need[r] = posted ? min(posted, 32u) : 32u;
@@ -911,11 +1011,11 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
       if (i >= D || !cell[r]) continue;
       const bool isnull = item[r] == 0xffffffffu;
       int rc = put_at(h, cell[r], t + i, isnull ? 0 : item[r], isnull, VL);
-      if (VL) vl_event(h, c, cell[r], 1);   /* planned positions: at most 8 per lane */
+      if (VL) seg_event<QF>(h, c, cell[r], 1);   /* planned positions: at most 8 per lane */
       if (rc == 1 && !isnull) {   /* its group gave up: hand the reserved pages back */
         const unsigned x = OURO_CQ_ID(item[r]);
         int before = atomicAdd(&h.chunk_free[x], (int)OURO_CQ_CNT(item[r]));
-        if (before <= 0 && before + (int)OURO_CQ_CNT(item[r]) >= 1) chunk_push<VL>(h, c, x);
+        if (before <= 0 && before + (int)OURO_CQ_CNT(item[r]) >= 1) chunk_push<QF>(h, c, x);
       }
       if (isnull) stat_add(h, c, OURO_ST_DEAD, 1);
     }
@@ -926,7 +1026,7 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
     for (unsigned k = rk; k < g; k += nl) {
       const unsigned x = range_chunk(h, cr, k);
       const int b = atomicAdd(&h.chunk_free[x], (int)ppc);
-      if (b <= 0 && b + (int)ppc >= 1) chunk_push<VL>(h, c, x);
+      if (b <= 0 && b + (int)ppc >= 1) chunk_push<QF>(h, c, x);
     }
     __syncwarp(vmask);
     if (g < m) {
@@ -936,7 +1036,7 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
         for (unsigned it = 0; it < h.spin_limit; ++it) {
           unsigned long long t2 = ld_acq(&q->tail.v), h2 = ld_acq(&q->head.v);
           if (h2 <= t2) break;
-          if (VL) vl_slot(h, c, h2 - 1, true);
+          seg_prepare<QF>(h, c, t2, h2 - 1);
           if (atomicCAS(&q->tail.v, t2, h2) == t2) { dt = t2; dn = h2 - t2; break; }
         }
         stat_add(h, c, OURO_ST_DEAD, dn);
@@ -944,10 +1044,10 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
       dt = __shfl_sync(vmask, dt, owner);
       dn = __shfl_sync(vmask, dn, owner);
       for (unsigned long long i = rk; i < dn; i += nl) {
-        unsigned long long *cl = slot_at<VL>(h, c, dt + i, true);
+        unsigned long long *cl = slot_at<QF>(h, c, dt + i, true);
         if (!cl) continue;
         put_at(h, cl, dt + i, 0, true, VL);
-        if (VL) vl_event(h, c, cl, 1);
+        if (VL) seg_event<QF>(h, c, cl, 1);
       }
       break;
     }
@@ -1015,7 +1115,8 @@ __device__ inline unsigned claim_pages(const ouro_heap_dev &h, unsigned x, unsig
 /* Every lane of vmask calls; lanes with cls < 0 only help (see page_malloc). */
 template <int V>
 __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
-  constexpr bool VL = (V == OURO_CHUNK_VLIST);
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
   const bool req = cls >= 0;
   ouro_qhdr *q = qh(h, req ? cls : 0);
   const unsigned lane = laneid();
@@ -1045,18 +1146,18 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
         posted = false;
         cell = nullptr;
       }
-      if (!cell) cell = slot_at<VL>(h, cls, pos, false);
+      if (!cell) cell = slot_at<QF>(h, cls, pos, false);
       unsigned item = 0;
       int r = cell ? try_take<VL>(h, cls, cell, pos, &item) : 0;
       if (r) {
-        if (VL) vl_event(h, cls, cell, 1);
+        if (VL) seg_event<QF>(h, cls, cell, 1);
         have = false;
         res = (unsigned)r;
         got_item = item;
       } else if (pos >= ld_acq(&q->tail.v)) {
         debt = true;
         if (!posted) {
-          if (!cell && VL) cell = vl_slot(h, cls, pos, true);
+          if (!cell && VL) cell = slot_at<QF>(h, cls, pos, true);
           if (cell) {
             const unsigned long long e = ld_acq(cell);
             const int d = slot_d(e, pos);
@@ -1066,7 +1167,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
         }
       }
       if (it >= h.spin_limit && !res) {                 /* bounded wait ran out */
-        if (!cell) cell = slot_at<VL>(h, cls, pos, true);
+        if (!cell) cell = slot_at<QF>(h, cls, pos, true);
         unsigned item2 = 0;
         int g = cell ? give_up<VL>(h, cls, cell, pos, &item2) : 0;
         if (g == 1 || g == 2) {
@@ -1077,7 +1178,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
           set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_CHUNK_GIVEUP);
           stat_add(h, cls, OURO_ST_CANCEL, 1);
         }
-        if (VL && cell && g) vl_event(h, cls, cell, 1);
+        if (VL && cell && g) seg_event<QF>(h, cls, cell, 1);
         have = false;
       }
     }
@@ -1120,17 +1221,17 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
           if (cnt > jneed) {   /* reserved for a warp-sized need that was not posted: hand back the rest */
             const int ex = (int)(cnt - jneed);
             const int b = atomicAdd(&h.chunk_free[x], ex);
-            if (b <= 0 && b + ex >= 1) chunk_push<(V == OURO_CHUNK_VLIST)>(h, jcls, x);
+            if (b <= 0 && b + ex >= 1) chunk_push<QF>(h, jcls, x);
           }
         } else {
           const int old = atomicSub(&h.chunk_free[x], (int)jneed);
           granted = old <= 0 ? 0 : min((unsigned)old, jneed);
           const int left = old - (int)jneed;
-          if (left >= 1) chunk_push<(V == OURO_CHUNK_VLIST)>(h, jcls, x);
+          if (left >= 1) chunk_push<QF>(h, jcls, x);
           if (granted < jneed) {
             const int ex = (int)(jneed - granted);
             const int b = atomicAdd(&h.chunk_free[x], ex);
-            if (b <= 0 && b + ex >= 1) chunk_push<(V == OURO_CHUNK_VLIST)>(h, jcls, x);
+            if (b <= 0 && b + ex >= 1) chunk_push<QF>(h, jcls, x);
           }
         }
       }
@@ -1170,7 +1271,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
 /* free into a chunk queue: every lane of mask calls; lanes with cls < 0 only take part */
 template <int V>
 __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, unsigned mask) {
-  constexpr bool VL = (V == OURO_CHUNK_VLIST);
+  constexpr int QF = ouro_qform(V);
   const unsigned lane = laneid();
   unsigned x = 0, pg = 0;
   if (cls >= 0) {
@@ -1198,7 +1299,7 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
     const int k = __popc(cg);
     __threadfence();
     const int b = atomicAdd(&h.chunk_free[x], k);
-    if (b <= 0 && b + k >= 1) chunk_push<VL>(h, cls, x);
+    if (b <= 0 && b + k >= 1) chunk_push<QF>(h, cls, x);
   }
   const unsigned sg = __match_any_sync(mask, cls);
   if (cls >= 0 && lane == (unsigned)(__ffs(sg) - 1)) stat_add(h, cls, OURO_ST_FREE, __popc(sg));
@@ -1320,7 +1421,7 @@ __device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev
   using namespace ouro::detail;
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   __syncwarp();
-  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) {
+  if constexpr (ouro_page_queues(V)) {
     for (unsigned c = 0; c < h.n_classes; ++c) {
       const unsigned n = ctx.cnt[w][c];
       if (!n) continue;
@@ -1354,6 +1455,8 @@ static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t 
     case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, mask);
     case OURO_CHUNK_ARRAY: return chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, mask);
     case OURO_CHUNK_VLIST: return chunk_malloc<OURO_CHUNK_VLIST>(h, cls, mask);
+    case OURO_PAGE_VARRAY: return page_malloc<OURO_PAGE_VARRAY>(h, cls, mask);
+    case OURO_CHUNK_VARRAY: return chunk_malloc<OURO_CHUNK_VARRAY>(h, cls, mask);
     default: return nullptr;
   }
 }
@@ -1368,7 +1471,7 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
   if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
-    else if (h.checked && (h.variant == OURO_PAGE_ARRAY || h.variant == OURO_PAGE_VLIST)) {
+    else if (h.checked && ouro_page_queues((int)h.variant)) {
       unsigned ppcm = (1u << (h.log2_chunk - 4 - cls)) - 1;
       unsigned pg = item & ppcm, x = item >> (h.log2_chunk - 4 - cls);
       unsigned bit = 1u << (pg & 31);
@@ -1379,11 +1482,13 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
   }
   if (h.variant == OURO_CHUNK_ARRAY) { chunk_free_impl<OURO_CHUNK_ARRAY>(h, cls, p, mask); return; }
   if (h.variant == OURO_CHUNK_VLIST) { chunk_free_impl<OURO_CHUNK_VLIST>(h, cls, p, mask); return; }
+  if (h.variant == OURO_CHUNK_VARRAY) { chunk_free_impl<OURO_CHUNK_VARRAY>(h, cls, p, mask); return; }
   const unsigned vmask = __ballot_sync(mask, cls >= 0);
   if (cls < 0) return;
   switch (h.variant) {
     case OURO_PAGE_ARRAY: page_free<OURO_PAGE_ARRAY>(h, cls, item, vmask); break;
     case OURO_PAGE_VLIST: page_free<OURO_PAGE_VLIST>(h, cls, item, vmask); break;
+    case OURO_PAGE_VARRAY: page_free<OURO_PAGE_VARRAY>(h, cls, item, vmask); break;
     default: break;
   }
 }

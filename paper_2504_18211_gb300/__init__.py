@@ -8,7 +8,7 @@ C entry points under the same names.
 from __future__ import annotations
 
 from . import _binding as B
-from ._binding import (CHUNK_ARRAY, CHUNK_VLIST, PAGE_ARRAY, PAGE_VLIST, VARIANTS, Options,  # noqa: F401
+from ._binding import (CHUNK_ARRAY, CHUNK_VARRAY, CHUNK_VLIST, PAGE_ARRAY, PAGE_VARRAY, PAGE_VLIST, VARIANTS, Options,  # noqa: F401
                        OuroError, check_to_dict, load, ouro_batch_free, ouro_batch_malloc,
                        ouro_debug_stall_producer, ouro_heap_create_ex, ouro_heap_destroy,
                        ouro_heap_device, ouro_heap_reset, ouro_heap_snapshot, ouro_heap_stats,

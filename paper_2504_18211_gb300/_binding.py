@@ -14,9 +14,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libouro.so")
 MAX_CLASSES = 17
 
-PAGE_ARRAY, CHUNK_ARRAY, PAGE_VLIST, CHUNK_VLIST = 0, 1, 2, 3
+PAGE_ARRAY, CHUNK_ARRAY, PAGE_VLIST, CHUNK_VLIST, PAGE_VARRAY, CHUNK_VARRAY = 0, 1, 2, 3, 4, 5
 VARIANTS = {"page_array": PAGE_ARRAY, "chunk_array": CHUNK_ARRAY,
-            "page_vlist": PAGE_VLIST, "chunk_vlist": CHUNK_VLIST}
+            "page_vlist": PAGE_VLIST, "chunk_vlist": CHUNK_VLIST,
+            "page_varray": PAGE_VARRAY, "chunk_varray": CHUNK_VARRAY}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EDEVICE", 5: "ENOTSUP"}
 ERR_BAD_FREE, ERR_DOUBLE_FREE, ERR_QUEUE_FULL, ERR_TIMEOUT, ERR_QUEUE_OVERFLOW = 1, 2, 4, 8, 16
 

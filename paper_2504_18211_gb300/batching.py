@@ -99,7 +99,7 @@ class BatchRun:
 
 
 def autotune(Heap, run: BatchRun, heap_bytes: int, chunks=(4096, 8192, 16384, 65536),
-             variants=("page_array", "page_vlist", "chunk_array", "chunk_vlist"),
+             variants=("page_array", "page_vlist", "chunk_array", "chunk_vlist", "page_varray", "chunk_varray"),
              warps_per_sm=(8, 16, 32, 48, 64), reps: int = 2, max_size: int = 8192):
     """Time the persistent form over chunk size x queue variant x warps per SM.
 

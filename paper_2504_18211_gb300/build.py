@@ -40,6 +40,8 @@ def _compile(src: str, extra=()) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    if extra and r.stderr:
+        print(r.stderr, file=sys.stderr)     # e.g. -Xptxas -v: registers, spills, shared memory
     return obj
 
 

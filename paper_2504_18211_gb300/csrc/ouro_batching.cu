@@ -119,6 +119,8 @@ extern "C" int ouro_batches_max_blocks_per_sm(const ouro_heap *H) {
     case OURO_PAGE_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_VLIST, false>, 256, 0); break;
     case OURO_CHUNK_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_ARRAY, false>, 256, 0); break;
     case OURO_CHUNK_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_VLIST, false>, 256, 0); break;
+    case OURO_PAGE_VARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_VARRAY, false>, 256, 0); break;
+    case OURO_CHUNK_VARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_VARRAY, false>, 256, 0); break;
     default: break;
   }
   return per_sm;

@@ -50,8 +50,9 @@ static inline unsigned long long next_pow2(unsigned long long x) {
   while (p < x) p <<= 1;
   return p;
 }
-static inline bool is_page(unsigned v) { return v == OURO_PAGE_ARRAY || v == OURO_PAGE_VLIST; }
-static inline bool is_vlist(unsigned v) { return v == OURO_PAGE_VLIST || v == OURO_CHUNK_VLIST; }
+static inline bool is_page(unsigned v) { return ouro_page_queues((int)v); }
+static inline bool is_virtual(unsigned v) { return ouro_qform((int)v) != OURO_QF_RING; }
+static inline bool is_varray(unsigned v) { return ouro_qform((int)v) == OURO_QF_VARRAY; }
 
 /* ------------------------------------------------------------- init kernels */
 __global__ void k_init_qhdr(ouro_heap_dev h) {
@@ -68,14 +69,16 @@ __global__ void k_init_qhdr(ouro_heap_dev h) {
   for (unsigned i = threadIdx.x; i < OURO_VL_HINTS; i += blockDim.x) q->hint[i] = pack(0, OURO_NIL);
 }
 
-/* every ring slot starts empty for its own position: seq = index */
+/* every ring slot starts empty for its own position (seq = index); every
+ * virtualized-array directory entry starts empty for segment index = entry */
 __global__ void k_init_cells(ouro_heap_dev h) {
+  const unsigned item = ouro_qform((int)h.variant) == OURO_QF_VARRAY ? OURO_NIL : 0u;
   for (int c = 0; c < (int)h.n_classes; ++c) {
     const unsigned long long R = h.ring_mask[c] + 1;
     unsigned long long *cells = h.cells + h.ring_off[c];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
          i += (unsigned long long)gridDim.x * blockDim.x)
-      cells[i] = slot(i, 0);
+      cells[i] = slot(i, item);
   }
 }
 
@@ -114,9 +117,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   *out = nullptr;
   if (chunk_bytes < 256 || chunk_bytes > (1u << 20) || (chunk_bytes & (chunk_bytes - 1))) return OURO_EINVAL;
   if (bytes == 0 || bytes % chunk_bytes || bytes > (64ull << 30)) return OURO_EINVAL;
-  if (variant != OURO_PAGE_ARRAY && variant != OURO_PAGE_VLIST && variant != OURO_CHUNK_ARRAY &&
-      variant != OURO_CHUNK_VLIST)
-    return OURO_EINVAL;
+  if (variant < OURO_PAGE_ARRAY || variant > OURO_CHUNK_VARRAY) return OURO_EINVAL;
   if (d_heap_buf && ((uintptr_t)d_heap_buf & 255)) return OURO_EINVAL;
   if (!is_page(variant) && bytes / chunk_bytes > (1ull << 26)) return OURO_EINVAL;   /* chunk id field: 26 bits */
 
@@ -160,7 +161,9 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   d.checked = o.checked ? 1u : 0u;
   d.staging = (o.staging && is_page(variant)) ? 1u : 0u;
 
-  /* ring sizes (array variants) */
+  /* ring sizes (plain arrays); directory sizes (virtualized arrays): a
+   * directory spans every position that can be live at once -- all items
+   * of the class, plus waiting and in-flight positions -- in whole segments */
   unsigned long long ring_total = 0;
   for (unsigned c = 0; c < d.n_classes; ++c) {
     unsigned long long cap = 0, R = 0;
@@ -171,6 +174,9 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
     } else if (variant == OURO_CHUNK_ARRAY) {
       cap = d.n_chunks;
       R = next_pow2(cap + OURO_RING_SLACK);
+    } else if (is_varray(variant)) {
+      const unsigned long long items = is_page(variant) ? bytes >> (4 + c) : d.n_chunks;
+      R = next_pow2((items + OURO_VA_SLACK + d.seg_cap - 1) / d.seg_cap + 4);
     }
     d.qcap[c] = cap;
     d.ring_off[c] = ring_total;
@@ -262,9 +268,8 @@ __global__ void k_count_queued(ouro_heap_dev h, unsigned long long *out) {
   ouro_qhdr *q = qh(h, c);
   const unsigned long long hd = q->head.v, tl = q->tail.v;
   unsigned long long n = 0;
-  const bool vl = h.variant == OURO_PAGE_VLIST || h.variant == OURO_CHUNK_VLIST;
   for (unsigned long long p = hd + threadIdx.x; p < tl; p += blockDim.x) {
-    unsigned long long *cell = vl ? vl_slot(h, c, p, false) : ring_slot(h, c, p);
+    unsigned long long *cell = slot_any(h, c, p);
     if (cell && slot_d(*cell, p) == 1) n++;
   }
   atomicAdd(&out[c], n);
@@ -275,14 +280,13 @@ __global__ void k_collect_queue(ouro_heap_dev h, int c, unsigned *out, unsigned 
                                 unsigned long long *n_out) {
   ouro_qhdr *q = qh(h, c);
   const unsigned long long hd = q->head.v, tl = q->tail.v;
-  const bool vl = h.variant == OURO_PAGE_VLIST || h.variant == OURO_CHUNK_VLIST;
   unsigned long long n = 0;
   for (unsigned long long p = hd; p < tl; ++p) {
-    unsigned long long *cell = vl ? vl_slot(h, c, p, false) : ring_slot(h, c, p);
+    unsigned long long *cell = slot_any(h, c, p);
     if (!cell) continue;
     unsigned long long v = *cell;
     if (slot_d(v, p) != 1) continue;
-    const bool cq = h.variant == OURO_CHUNK_ARRAY || h.variant == OURO_CHUNK_VLIST;
+    const bool cq = !ouro_page_queues((int)h.variant);
     if (n < cap) out[n] = cq ? OURO_CQ_ID(lo32(v)) : lo32(v);
     n++;
   }
@@ -344,7 +348,7 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
   OURO_LAUNCHED();
   k_chunk_hist<<<2 * sm_count(), 256, 0, s>>>(d, dh);
   OURO_LAUNCHED();
-  if (is_vlist(d.variant)) {
+  if (is_virtual(d.variant)) {
     k_count_spares<<<1, 32, 0, s>>>(d, ds);
     OURO_LAUNCHED();
   }
@@ -442,15 +446,14 @@ extern "C" void ouro_snapshot_free(ouro_snapshot *sn) {
 /* -------------------------------------------------------------------- trim */
 /* 1. count the queued pages of every chunk (page queues) */
 __global__ void k_trim_count(ouro_heap_dev h, unsigned *qcount) {
-  if (h.variant == OURO_CHUNK_ARRAY || h.variant == OURO_CHUNK_VLIST) return;   /* counts live in chunk_free */
+  if (!ouro_page_queues((int)h.variant)) return;   /* counts live in chunk_free */
   const int c = blockIdx.y;
   ouro_qhdr *q = qh(h, c);
   const unsigned long long hd = q->head.v, tl = q->tail.v;
   const unsigned ppc_log = h.log2_chunk - 4 - c;
-  const bool vl = h.variant == OURO_PAGE_VLIST;
   for (unsigned long long p = hd + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < tl;
        p += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned long long *cell = vl ? vl_slot(h, c, p, false) : ring_slot(h, c, p);
+    unsigned long long *cell = slot_any(h, c, p);
     if (!cell) continue;
     unsigned long long v = *cell;
     if (slot_d(v, p) == 1) atomicAdd(&qcount[lo32(v) >> ppc_log], 1u);
@@ -497,8 +500,7 @@ __global__ void k_trim_compact(ouro_heap_dev h, int c, const unsigned char *in_p
   ouro_qhdr *q = qh(h, c);
   const unsigned long long hd = q->head.v, tl = q->tail.v;
   const unsigned ppc_log = h.log2_chunk - 4 - c;
-  const bool vl = h.variant == OURO_PAGE_VLIST || h.variant == OURO_CHUNK_VLIST;
-  const bool cq = h.variant == OURO_CHUNK_ARRAY || h.variant == OURO_CHUNK_VLIST;
+  const bool cq = !ouro_page_queues((int)h.variant);
   __shared__ unsigned warp_tot[32];
   __shared__ unsigned long long base;
   if (threadIdx.x == 0) base = 0;
@@ -509,7 +511,7 @@ __global__ void k_trim_compact(ouro_heap_dev h, int c, const unsigned char *in_p
     unsigned item = 0;
     bool keep = false;
     if (p < tl) {
-      unsigned long long *cell = vl ? vl_slot(h, c, p, false) : ring_slot(h, c, p);
+      unsigned long long *cell = slot_any(h, c, p);
       if (cell) {
         unsigned long long v = *cell;
         if (slot_d(v, p) == 1) {
@@ -602,12 +604,23 @@ __global__ void k_trim_carved(ouro_heap_dev h, const unsigned long long *hist) {
   for (unsigned c = threadIdx.x; c < h.n_classes; c += blockDim.x) qh(h, c)->carved.v = hist[c];
 }
 
-/* list relay: one block per class call; thread 0 links segments from the pool */
+/* virtualized-array directory: every entry empty for its own index */
+__global__ void k_trim_reset_dir(ouro_heap_dev h, int c) {
+  const unsigned long long D = h.ring_mask[c] + 1;
+  unsigned long long *dir = h.cells + h.ring_off[c];
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < D;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dir[i] = pack((unsigned)i, OURO_NIL);
+}
+
+/* virtualized relay: one block per class call; thread 0 takes segments from
+ * the pool and links them (list) or enters them in the directory (array) */
 __global__ void k_trim_relay_list(ouro_heap_dev h, int c, const unsigned *tmp, const unsigned long long *n_in) {
   __shared__ unsigned seg_chunk;
   ouro_qhdr *q = qh(h, c);
   const unsigned long long n = *n_in;
   const unsigned cap = h.seg_cap;
+  const bool dir = ouro_qform((int)h.variant) == OURO_QF_VARRAY;
   unsigned prev = OURO_NIL;
   for (unsigned long long s = 0; s * cap < n; ++s) {
     if (threadIdx.x == 0) {
@@ -617,9 +630,13 @@ __global__ void k_trim_relay_list(ouro_heap_dev h, int c, const unsigned *tmp, c
         h.chunk_cls[x] = OURO_CLS_SEG;
         seg_of(h, x)->link = pack((unsigned)s, OURO_NIL);
         seg_of(h, x)->done = 0;
-        if (prev == OURO_NIL) q->front.v = pack((unsigned)s, x);
-        else seg_of(h, prev)->link = pack((unsigned)(s - 1), x);
-        q->back.v = pack((unsigned)s, x);
+        if (dir) {
+          *va_entry(h, c, s) = pack((unsigned)s, x);
+        } else {
+          if (prev == OURO_NIL) q->front.v = pack((unsigned)s, x);
+          else seg_of(h, prev)->link = pack((unsigned)(s - 1), x);
+          q->back.v = pack((unsigned)s, x);
+        }
       } else {
         set_error(h, OURO_ERR_QUEUE_FULL, OURO_SITE_TRIM);
       }
@@ -690,6 +707,10 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
     } else {
       k_trim_reset_q<<<1, 1, 0, s>>>(d, (int)c, ncount + c);
       OURO_LAUNCHED();
+      if (is_varray(d.variant)) {
+        k_trim_reset_dir<<<grid, 256, 0, s>>>(d, (int)c);
+        OURO_LAUNCHED();
+      }
       k_trim_relay_list<<<1, 256, 0, s>>>(d, (int)c, src, ncount + c);
       OURO_LAUNCHED();
     }
@@ -780,7 +801,7 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
   OURO_LAUNCHED();
   k_chunk_hist<<<2 * sm_count(), 256, 0, s>>>(d, dh);
   OURO_LAUNCHED();
-  if (is_vlist(d.variant)) {
+  if (is_virtual(d.variant)) {
     k_count_spares<<<1, 32, 0, s>>>(d, ds);
     OURO_LAUNCHED();
   }

@@ -11,6 +11,9 @@
  * (152 SMs x 2048), so a ring of (capacity + slack) slots never makes a
  * producer wait for a consumer that is still in flight one lap behind. */
 #define OURO_RING_SLACK (1ull << 19)
+/* virtualized-array directories also span positions that are waiting for a
+ * producer or in flight (more than twice the resident threads of 152 SMs) */
+#define OURO_VA_SLACK (1ull << 20)
 
 struct ouro_heap {
   ouro_heap_dev d;

@@ -10,8 +10,6 @@ namespace ouro {
 namespace detail {
 
 
-/* Staged malloc / free: page queues use the warp's shared-memory stacks;
- * chunk queues go to the heap. */
 /* Variant-resolved malloc.  want = false: the lane asks for nothing but
  * stays in the call to help its warp carve (see page_malloc). */
 template <int V>
@@ -20,7 +18,7 @@ __device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long 
   const int cls = want ? size_class(h, n) : -1;
   if (want && cls < 0) stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
   if (!__any_sync(mask, cls >= 0)) return nullptr;
-  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) return page_malloc<V>(h, cls, mask);
+  if constexpr (ouro_page_queues(V)) return page_malloc<V>(h, cls, mask);
   else return chunk_malloc<V>(h, cls, mask);
 }
 
@@ -32,7 +30,7 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
   if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
-    else if (h.checked && (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST)) {
+    else if (h.checked && ouro_page_queues(V)) {
       const unsigned sh = h.log2_chunk - 4 - cls;
       const unsigned pg = item & ((1u << sh) - 1), x = item >> sh, bit = 1u << (pg & 31);
       __threadfence();
@@ -43,7 +41,7 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
       }
     }
   }
-  if constexpr (V == OURO_CHUNK_ARRAY || V == OURO_CHUNK_VLIST) {
+  if constexpr (!ouro_page_queues(V)) {
     chunk_free_impl<V>(h, cls, p, mask);
   } else {
     const unsigned vmask = __ballot_sync(mask, cls >= 0);
@@ -52,16 +50,18 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
   }
 }
 
+/* Staged malloc / free: page queues use the warp's shared-memory stacks;
+ * chunk queues go to the heap. */
 template <int V, int WARPS>
 __device__ __forceinline__ void *stage_malloc_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h,
                                                 unsigned long long n, bool want) {
-  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) return ouro::detail::stage_malloc<V, WARPS>(ctx, h, n, want);
+  if constexpr (ouro_page_queues(V)) return ouro::detail::stage_malloc<V, WARPS>(ctx, h, n, want);
   else return malloc_v<V>(h, n, want);
 }
 
 template <int V, int WARPS>
 __device__ __forceinline__ void stage_free_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
-  if constexpr (V == OURO_PAGE_ARRAY || V == OURO_PAGE_VLIST) ouro::detail::stage_free<V, WARPS>(ctx, h, p);
+  if constexpr (ouro_page_queues(V)) ouro::detail::stage_free<V, WARPS>(ctx, h, p);
   else free_v<V>(h, p);
 }
 
@@ -245,6 +245,8 @@ __device__ inline void warp_flush(payload_acc &a, unsigned long long nulls, ouro
     case OURO_PAGE_VLIST: { constexpr int V = OURO_PAGE_VLIST; CALL; break; }   \
     case OURO_CHUNK_ARRAY: { constexpr int V = OURO_CHUNK_ARRAY; CALL; break; } \
     case OURO_CHUNK_VLIST: { constexpr int V = OURO_CHUNK_VLIST; CALL; break; } \
+    case OURO_PAGE_VARRAY: { constexpr int V = OURO_PAGE_VARRAY; CALL; break; } \
+    case OURO_CHUNK_VARRAY: { constexpr int V = OURO_CHUNK_VARRAY; CALL; break; } \
     default: return OURO_ENOTSUP;                                                \
   }
 

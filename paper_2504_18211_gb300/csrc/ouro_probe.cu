@@ -95,6 +95,8 @@ extern "C" ouro_status ouro_malloc_latency(ouro_heap *H, const uint32_t *d_sizes
     case OURO_PAGE_VLIST: k_malloc_timed<OURO_PAGE_VLIST><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
     case OURO_CHUNK_ARRAY: k_malloc_timed<OURO_CHUNK_ARRAY><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
     case OURO_CHUNK_VLIST: k_malloc_timed<OURO_CHUNK_VLIST><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
+    case OURO_PAGE_VARRAY: k_malloc_timed<OURO_PAGE_VARRAY><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
+    case OURO_CHUNK_VARRAY: k_malloc_timed<OURO_CHUNK_VARRAY><<<(int)g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n, d_hist); break;
     default: return OURO_ENOTSUP;
   }
   OURO_LAUNCHED();

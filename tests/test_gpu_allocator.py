@@ -1,4 +1,4 @@
-"""GPU parity of the allocator (page / chunk queues, array / virtualized list) against the oracle.
+"""GPU parity of the allocator (page / chunk queues; plain array, virtualized list, virtualized array) against the oracle.
 
 Every test calls the CUDA library through its C ABI (paper_2504_18211_gb300
 binding) and compares with oracle/ on the same seeded inputs:
@@ -19,8 +19,8 @@ from gpu_helpers import (assert_no_overlap, oracle_round, per_class_counts,
 from paper_2504_18211_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-PAGE_VARIANTS = ("page_array", "page_vlist")
-ALL_VARIANTS = ("page_array", "page_vlist", "chunk_array", "chunk_vlist")
+PAGE_VARIANTS = ("page_array", "page_vlist", "page_varray")
+ALL_VARIANTS = ("page_array", "page_vlist", "chunk_array", "chunk_vlist", "page_varray", "chunk_varray")
 
 
 def carve_bounds_ok(variant, got, want, sizes, chunk):
@@ -155,8 +155,8 @@ def test_sweep_fused_rounds(ouro, variant, staging):
 
 @pytest.mark.parametrize("variant", ALL_VARIANTS)
 def test_single_class_fill_to_exhaustion(ouro, variant):
-    """A full heap answers null exactly as often as the oracle (array queues);
-    virtualized lists also spend chunks on queue segments (bounded)."""
+    """A full heap answers null exactly as often as the oracle (plain array
+    queues); virtualized queues also spend chunks on queue segments."""
     torch = torch_cuda()
     bytes_, chunk, size = 64 * 4096, 4096, 256
     cap = bytes_ // size
@@ -171,7 +171,7 @@ def test_single_class_fill_to_exhaustion(ouro, variant):
         ok = int((p != 0).sum())
         assert_no_overlap(p, sizes, heap.base, bytes_, chunk)
         st = heap.stats()
-        if variant.endswith("array"):
+        if variant in ("page_array", "chunk_array"):
             assert ok == o_ok == cap
         else:
             segs = st["seg_chunks"] + st["spare_chunks"]

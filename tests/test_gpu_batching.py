@@ -32,7 +32,8 @@ def oracle_checks(sizes, offs, seed, chunk, variant):
     return out
 
 
-@pytest.mark.parametrize("variant", ["page_array", "page_vlist", "chunk_array", "chunk_vlist"])
+@pytest.mark.parametrize("variant", ["page_array", "page_vlist", "chunk_array", "chunk_vlist", "page_varray",
+                                     "chunk_varray"])
 @pytest.mark.parametrize("chunk", [8192, 4096])
 def test_batching_forms_match_oracle(P, variant, chunk):
     from paper_2504_18211_gb300.batching import FORMS, BatchRun
@@ -77,7 +78,7 @@ def test_persistent_form_is_one_launch_and_graph_replays(P):
         run.close()
 
 
-@pytest.mark.parametrize("variant", ["page_array", "page_vlist"])
+@pytest.mark.parametrize("variant", ["page_array", "page_vlist", "page_varray"])
 def test_persistent_form_with_staging(P, variant):
     """Shared-memory staging in the persistent kernel: same per-batch checks
     as the oracle, every page back in its queue at the end."""

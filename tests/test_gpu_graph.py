@@ -23,7 +23,7 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist"])
+@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray"])
 def test_graph_growth_matches_edge_list_and_closed_form(P, variant):
     from paper_2504_18211_gb300.graph import GraphRun, expected_class_counts
     torch = torch_cuda()

@@ -29,7 +29,7 @@ def session_checksum(seed, s, nblocks, block_bytes):
     return r["xor64"], r["sum64"]
 
 
-@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist"])
+@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray"])
 def test_serving_loop_matches_model_and_oracle(P, variant):
     from paper_2504_18211_gb300.serving import ServeRun, model_schedule
     torch_cuda()

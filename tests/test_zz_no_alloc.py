@@ -23,7 +23,7 @@ def _stats_via_abi(lib, h, fn_name, stream):
     return B._stats_dict(s)
 
 
-@pytest.mark.parametrize("variant", ["page_array", "page_vlist"])
+@pytest.mark.parametrize("variant", ["page_array", "page_vlist", "page_varray"])
 def test_static_stats_match_allocating_stats(variant):
     import torch
 
