@@ -276,18 +276,8 @@ __device__ inline unsigned spare_pop(const ouro_heap_dev &h, int c) {
   return OURO_NIL;
 }
 
-/* A fresh segment with index idx: spare of the class first, else a chunk of
- * the heap.  Every slot starts empty for its own position. */
-__device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) {
-  unsigned x = spare_pop(h, c);
-  const bool fresh = x == OURO_NIL;
-  if (fresh) {
-    chunk_range r = take_chunks(h, 1);
-    if (r.k1 + r.k2 == 0) return OURO_NIL;
-    x = range_chunk(h, r, 0);
-    h.chunk_cls[x] = OURO_CLS_SEG;
-    stat_add(h, c, OURO_ST_SEG, 1);
-  }
+/* Set chunk x up as segment idx: every slot reads empty for its own position. */
+__device__ inline void seg_init(const ouro_heap_dev &h, unsigned x, unsigned idx, bool fresh) {
   ouro_seg *s = seg_of(h, x);
   s->done = 0;
   /* A segment recycled from the spare stack always serves a higher index, so
@@ -311,6 +301,21 @@ __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) 
   }
   s->link = pack(idx, OURO_NIL);
   __threadfence();
+}
+
+/* A fresh segment with index idx: spare of the class first, else a chunk of
+ * the heap. */
+__device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) {
+  unsigned x = spare_pop(h, c);
+  const bool fresh = x == OURO_NIL;
+  if (fresh) {
+    chunk_range r = take_chunks(h, 1);
+    if (r.k1 + r.k2 == 0) return OURO_NIL;
+    x = range_chunk(h, r, 0);
+    h.chunk_cls[x] = OURO_CLS_SEG;
+    stat_add(h, c, OURO_ST_SEG, 1);
+  }
+  seg_init(h, x, idx, fresh);
   return x;
 }
 
@@ -351,6 +356,24 @@ __device__ inline void va_retire(const ouro_heap_dev &h, int c, unsigned x) {
   spare_push(h, c, x);
 }
 
+/* Look-ahead for producers in the second half of segment s - 1: set up
+ * segment s from the class spare stack (never from the heap, so exhaustion
+ * is unchanged) if nobody has, so that the producers reaching it do not wait
+ * for its creation. */
+__device__ inline void va_prefetch(const ouro_heap_dev &h, int c, unsigned s32) {
+  unsigned long long *e = va_entry(h, c, s32);
+  const unsigned long long v = pack(s32, OURO_NIL);
+  if (ld_rlx(e) != v || lo32(ld_rlx(&qh(h, c)->spare.v)) == OURO_NIL) return;
+  if (cas_ar(e, v, pack(s32, OURO_BUSY)) != v) return;
+  const unsigned x = spare_pop(h, c);
+  if (x == OURO_NIL) {
+    st_rel(e, v);
+    return;
+  }
+  seg_init(h, x, s32, false);
+  st_rel(e, pack(s32, x));
+}
+
 /* Slot of position pos in the virtualized array of class c.  create: make
  * the segment if it does not exist (one creator, the others wait);
  * otherwise null while it does not exist.  Null too for a segment that has
@@ -368,7 +391,10 @@ __device__ inline unsigned long long *va_slot(const ouro_heap_dev &h, int c, uns
     const int d = (int)(hi32(v) - s32);
     const unsigned x = lo32(v);
     if (d > 0) return nullptr;
-    if (d == 0 && x < OURO_BUSY) return seg_cells(h, x) + off;
+    if (d == 0 && x < OURO_BUSY) {
+      if (create && off >= (h.seg_cap >> 1)) va_prefetch(h, c, s32 + 1);
+      return seg_cells(h, x) + off;
+    }
     if (!create) return nullptr;
     if (d == 0 && x == OURO_NIL) {
       if (cas_ar(e, v, pack(s32, OURO_BUSY)) == v) {
@@ -423,6 +449,27 @@ __device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsig
   }
 }
 
+/* Look-ahead for producers in the second half of segment cur = (idx, x):
+ * link its successor from the class spare stack (never from the heap) if it
+ * has none yet, so that the producers reaching it find it linked. */
+__device__ inline void vl_prefetch(const ouro_heap_dev &h, int c, unsigned long long cur) {
+  ouro_qhdr *q = qh(h, c);
+  ouro_seg *sg = seg_of(h, lo32(cur));
+  const unsigned long long link = pack(hi32(cur), OURO_NIL);
+  if (ld_rlx(&sg->link) != link || lo32(ld_rlx(&q->spare.v)) == OURO_NIL) return;
+  if (cas_ar(&sg->link, link, pack(hi32(cur), OURO_BUSY)) != link) return;
+  const unsigned x = spare_pop(h, c);
+  if (x == OURO_NIL) {
+    st_rel(&sg->link, link);
+    return;
+  }
+  seg_init(h, x, hi32(cur) + 1, false);
+  st_rel(&sg->link, pack(hi32(cur), x));
+  cas_ar(&q->back.v, cur, pack(hi32(cur) + 1, x));
+  __threadfence();
+  vl_advance(h, c);
+}
+
 /* Slot of position pos in the virtualized list of class c.  create: link
  * missing segments (producers); otherwise null while the segment is not
  * linked yet.  One thread creates each segment: it first claims the empty
@@ -434,8 +481,10 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
   const unsigned s32 = (unsigned)s;
   const unsigned off = (unsigned)(pos - s * h.seg_cap);
   unsigned long long e = ld_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)]);
-  if (hi32(e) == s32 && lo32(e) < OURO_BUSY && hi32(ld_acq(&seg_of(h, lo32(e))->link)) == s32)
+  if (hi32(e) == s32 && lo32(e) < OURO_BUSY && hi32(ld_acq(&seg_of(h, lo32(e))->link)) == s32) {
+    if (create && off >= (h.seg_cap >> 1)) vl_prefetch(h, c, e);
     return seg_cells(h, lo32(e)) + off;
+  }
   unsigned ns = h.backoff_min_ns;
   unsigned long long cur = 0;
   bool walking = false;
@@ -470,6 +519,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
     }
     if (hi32(cur) == s32) {
       st_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)], cur);
+      if (create && off >= (h.seg_cap >> 1)) vl_prefetch(h, c, cur);
       return seg_cells(h, lo32(cur)) + off;
     }
     ouro_seg *sg = seg_of(h, lo32(cur));
