@@ -47,6 +47,7 @@
 #define OURO_NSTAT 8
 #define OURO_SHARDS 32
 #define OURO_SEG_HDR 64
+#define OURO_AHEAD_POS (1ull << 20)   /* recycled segments go at most this many positions past the tail */
 
 /* queue storage forms */
 #define OURO_QF_RING 0     /* plain array: a ring of slots outside the heap */
@@ -146,6 +147,11 @@ __device__ __forceinline__ unsigned long long cas_rel(unsigned long long *p, uns
   unsigned long long o;
   asm volatile("atom.release.gpu.global.cas.b64 %0, [%1], %2, %3;"
                : "=l"(o) : "l"(p), "l"(c), "l"(v) : "memory");
+  return o;
+}
+__device__ __forceinline__ unsigned long long exch_rel(unsigned long long *p, unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(o) : "l"(p), "l"(v) : "memory");
   return o;
 }
 __device__ __forceinline__ unsigned long long cas_ar(unsigned long long *p, unsigned long long c,
@@ -319,8 +325,35 @@ __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) 
   return x;
 }
 
+/* A retired list segment x is appended behind the back segment (ahead of
+ * the producers, at most OURO_AHEAD_POS positions past the tail), so that
+ * producers find their segments linked; else it joins the spare stack. */
+__device__ inline void vl_recycle(const ouro_heap_dev &h, int c, unsigned x) {
+  ouro_qhdr *q = qh(h, c);
+  for (int k = 0; k < 8; ++k) {
+    const unsigned long long b = ld_acq(&q->back.v);
+    const unsigned bx = lo32(b);
+    if (bx >= OURO_BUSY) break;
+    ouro_seg *sg = seg_of(h, bx);
+    const unsigned long long link = ld_acq(&sg->link);
+    if (hi32(link) != hi32(b)) continue;                 /* stale back hint */
+    if (lo32(link) < OURO_BUSY) {                        /* a successor exists: move the hint on */
+      cas_ar(&q->back.v, b, pack(hi32(b) + 1, lo32(link)));
+      continue;
+    }
+    if (lo32(link) == OURO_BUSY) break;                  /* another thread is appending */
+    if ((unsigned long long)hi32(b) * h.seg_cap > ld_rlx(&q->tail.v) + OURO_AHEAD_POS) break;
+    if (cas_ar(&sg->link, link, pack(hi32(b), OURO_BUSY)) != link) continue;
+    seg_init(h, x, hi32(b) + 1, false);
+    st_rel(&sg->link, pack(hi32(b), x));
+    cas_ar(&q->back.v, b, pack(hi32(b) + 1, x));
+    return;
+  }
+  spare_push(h, c, x);
+}
+
 /* Retire fully used front segments (all slots produced and consumed, and a
- * successor linked) onto the class spare stack. */
+ * successor linked): each is recycled behind the back (or spared). */
 __device__ inline void vl_advance(const ouro_heap_dev &h, int c) {
   ouro_qhdr *q = qh(h, c);
   for (int i = 0; i < 64; ++i) {
@@ -334,7 +367,7 @@ __device__ inline void vl_advance(const ouro_heap_dev &h, int c) {
     if (ld_acq32(&seg_of(h, fx)->done) != 2u * h.seg_cap) return;
     unsigned long long nf = pack(hi32(f) + 1, nxt);
     cas_ar(&q->back.v, f, nf);           /* never leave the back hint on a retired segment */
-    if (cas_ar(&q->front.v, f, nf) == f) spare_push(h, c, fx);
+    if (cas_ar(&q->front.v, f, nf) == f) vl_recycle(h, c, fx);
   }
 }
 
@@ -349,14 +382,34 @@ __device__ __forceinline__ unsigned long long *va_entry(const ouro_heap_dev &h, 
 }
 
 /* Segment x has seen all its position events: its entry is emptied for the
- * next lap (index + D) and the chunk joins the class spare stack. */
+ * next lap (index + D), and the chunk is set up again as the first missing
+ * segment ahead of the producers (a burst of producers then finds its
+ * segments in place); the class front line keeps (next index << 32) as the
+ * place to look.  With no missing entry close enough ahead (within D/2
+ * segments, or OURO_AHEAD_POS positions, of the tail) it joins the spare
+ * stack. */
 __device__ inline void va_retire(const ouro_heap_dev &h, int c, unsigned x) {
+  ouro_qhdr *q = qh(h, c);
   const unsigned idx = hi32(ld_acq(&seg_of(h, x)->link));
-  st_rel(va_entry(h, c, idx), pack(idx + (unsigned)(h.ring_mask[c] + 1), OURO_NIL));
+  const unsigned long long D = h.ring_mask[c] + 1;
+  st_rel(va_entry(h, c, idx), pack(idx + (unsigned)D, OURO_NIL));
+  const unsigned long long tail = ld_rlx(&q->tail.v), ts = tail / h.seg_cap;
+  const unsigned long long lim = ts + min(D >> 1, OURO_AHEAD_POS / h.seg_cap + 1);
+  unsigned long long sn = max(ts + 1, (unsigned long long)hi32(ld_rlx(&q->front.v)));
+  for (int k = 0; k < 8 && sn < lim; ++k, ++sn) {
+    unsigned long long *e = va_entry(h, c, sn);
+    const unsigned long long v = pack((unsigned)sn, OURO_NIL);
+    if (ld_rlx(e) != v) continue;
+    if (cas_ar(e, v, pack((unsigned)sn, OURO_BUSY)) != v) continue;
+    seg_init(h, x, (unsigned)sn, false);
+    st_rel(e, pack((unsigned)sn, x));
+    atomicMax(&q->front.v, pack((unsigned)(sn + 1), OURO_NIL));
+    return;
+  }
   spare_push(h, c, x);
 }
 
-/* Look-ahead for producers in the second half of segment s - 1: set up
+/* Look-ahead for producers early in segment s - 1: set up
  * segment s from the class spare stack (never from the heap, so exhaustion
  * is unchanged) if nobody has, so that the producers reaching it do not wait
  * for its creation. */
@@ -392,7 +445,7 @@ __device__ inline unsigned long long *va_slot(const ouro_heap_dev &h, int c, uns
     const unsigned x = lo32(v);
     if (d > 0) return nullptr;
     if (d == 0 && x < OURO_BUSY) {
-      if (create && off >= (h.seg_cap >> 1)) va_prefetch(h, c, s32 + 1);
+      if (create && off - (h.seg_cap >> 3) < 32u) va_prefetch(h, c, s32 + 1);
       return seg_cells(h, x) + off;
     }
     if (!create) return nullptr;
@@ -449,7 +502,7 @@ __device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsig
   }
 }
 
-/* Look-ahead for producers in the second half of segment cur = (idx, x):
+/* Look-ahead for producers early in segment cur = (idx, x):
  * link its successor from the class spare stack (never from the heap) if it
  * has none yet, so that the producers reaching it find it linked. */
 __device__ inline void vl_prefetch(const ouro_heap_dev &h, int c, unsigned long long cur) {
@@ -482,7 +535,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
   const unsigned off = (unsigned)(pos - s * h.seg_cap);
   unsigned long long e = ld_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)]);
   if (hi32(e) == s32 && lo32(e) < OURO_BUSY && hi32(ld_acq(&seg_of(h, lo32(e))->link)) == s32) {
-    if (create && off >= (h.seg_cap >> 1)) vl_prefetch(h, c, e);
+    if (create && off - (h.seg_cap >> 3) < 32u) vl_prefetch(h, c, e);
     return seg_cells(h, lo32(e)) + off;
   }
   unsigned ns = h.backoff_min_ns;
@@ -519,7 +572,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
     }
     if (hi32(cur) == s32) {
       st_rlx(&q->hint[s32 & (OURO_VL_HINTS - 1)], cur);
-      if (create && off >= (h.seg_cap >> 1)) vl_prefetch(h, c, cur);
+      if (create && off - (h.seg_cap >> 3) < 32u) vl_prefetch(h, c, cur);
       return seg_cells(h, lo32(cur)) + off;
     }
     ouro_seg *sg = seg_of(h, lo32(cur));
@@ -591,6 +644,12 @@ __device__ inline void seg_prepare(const ouro_heap_dev &h, int c, unsigned long 
 __device__ inline int put_at(const ouro_heap_dev &h, unsigned long long *cell, unsigned long long pos,
                              unsigned item, bool null_marker, bool single_use = false) {
   const unsigned long long want = null_marker ? slot(pos + 2, 0) : slot(pos + 1, item);
+  if (single_use) {
+    /* a single-use slot only ever holds: a stale sequence or a posted need
+     * (empty), or the retired mark of a consumer that gave the position up;
+     * one exchange publishes the answer, and the old value tells which */
+    return slot_d(exch_rel(cell, want), pos) >= 3 ? 1 : 0;
+  }
   unsigned long long expect = slot(pos, 0);
   unsigned ns = h.backoff_min_ns;
   for (unsigned it = 0; it < h.spin_limit; ++it) {
