@@ -347,6 +347,7 @@ __device__ inline void vl_recycle(const ouro_heap_dev &h, int c, unsigned x) {
     seg_init(h, x, hi32(b) + 1, false);
     st_rel(&sg->link, pack(hi32(b), x));
     cas_ar(&q->back.v, b, pack(hi32(b) + 1, x));
+    st_rlx(&q->hint[(hi32(b) + 1) & (OURO_VL_HINTS - 1)], pack(hi32(b) + 1, x));
     return;
   }
   spare_push(h, c, x);
@@ -519,6 +520,7 @@ __device__ inline void vl_prefetch(const ouro_heap_dev &h, int c, unsigned long 
   seg_init(h, x, hi32(cur) + 1, false);
   st_rel(&sg->link, pack(hi32(cur), x));
   cas_ar(&q->back.v, cur, pack(hi32(cur) + 1, x));
+  st_rlx(&q->hint[(hi32(cur) + 1) & (OURO_VL_HINTS - 1)], pack(hi32(cur) + 1, x));
   __threadfence();
   vl_advance(h, c);
 }

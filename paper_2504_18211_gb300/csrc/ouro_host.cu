@@ -198,6 +198,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   H->off_free = off;  if (need_free) off = align256(off + d.n_chunks * 4);
   H->off_bits = off;  if (need_bits) off = align256(off + d.n_chunks * (size_t)d.words_per_chunk * 4);
   H->off_cells = off; off = align256(off + ring_total * 8);
+  H->off_work = off;  off = align256(off + OURO_WORK_SLOTS * 128);
   H->meta_bytes = off;
 
   cudaError_t e = cudaMalloc((void **)&H->meta, H->meta_bytes);

@@ -14,6 +14,9 @@
 /* virtualized-array directories also span positions that are waiting for a
  * producer or in flight (more than twice the resident threads of 152 SMs) */
 #define OURO_VA_SLACK (1ull << 20)
+/* work counters of fused rounds: one per launch in flight on a heap, each on
+ * its own 128-byte line, handed out round robin */
+#define OURO_WORK_SLOTS 64
 
 struct ouro_heap {
   ouro_heap_dev d;
@@ -22,7 +25,8 @@ struct ouro_heap {
   int owns_heap;
   unsigned char *meta;          /* one device allocation for every metadata table */
   size_t meta_bytes;
-  size_t off_qhdr, off_glob, off_stats, off_cls, off_pool, off_free, off_bits, off_cells;
+  size_t off_qhdr, off_glob, off_stats, off_cls, off_pool, off_free, off_bits, off_cells, off_work;
+  unsigned work_seq;            /* next work-counter slot (atomic) */
   size_t stats_words;
   unsigned long long ring_total;
   ouro_options opt;

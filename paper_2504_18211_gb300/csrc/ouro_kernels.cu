@@ -47,20 +47,26 @@ __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, ui
   if (OP & PAY_CHECK) flush_acc(a, nulls, out);
 }
 
-/* one whole round per thread: malloc, write, read back, free.  STAGE: the
- * warp's freed pages serve its next mallocs of the same class from shared
- * memory (page queues, heap option `staging`). */
+/* one whole round per thread: malloc, write, read back, free.  Warps pull
+ * 32 requests at a time from the launch's work counter, so blocks of
+ * uneven sizes balance across warps and the round ends within one task of
+ * the last byte.  STAGE: the warp's freed pages serve its next mallocs of
+ * the same class from shared memory (page queues, heap option `staging`). */
 template <int V, bool STAGE>
 __global__ void __launch_bounds__(256, 4) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
-                                                     uint32_t seed, int mode, ouro_check *out, void **ptrs) {
+                                                     uint32_t seed, int mode, ouro_check *out, void **ptrs,
+                                                     unsigned long long *work) {
   __shared__ ouro_block_ctx<8> ctx;
   if (STAGE) ouro_block_begin(ctx);
   payload_acc a;
   unsigned long long nulls = 0;
-  const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
-  const size_t wid = (((size_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5;
-  for (size_t base = wid * 32; base < n; base += warps * 32) {
-    const size_t i = base + (threadIdx.x & 31);
+  const unsigned lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    const size_t i = base + lane;
     const uint32_t sz = i < n ? sizes[i] : 0;
     unsigned char *p = nullptr;
     if (STAGE) {
@@ -154,13 +160,20 @@ extern "C" ouro_status ouro_round_fused(ouro_heap *H, const uint32_t *d_sizes, s
   if (mode != 0 && mode != 1) return OURO_EINVAL;
   OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
   if (!n) return OURO_OK;
+  /* this launch's work counter: a slot of the heap's ring, zeroed on the
+   * launch's stream (launches in flight at once on one heap: up to 64) */
+  const unsigned slot = __atomic_fetch_add(&H->work_seq, 1u, __ATOMIC_RELAXED) % OURO_WORK_SLOTS;
+  unsigned long long *work = (unsigned long long *)(H->meta + H->off_work + (size_t)slot * 128);
+  OURO_CUDA(cudaMemsetAsync(work, 0, 8, S(stream)));
   const int block = 256;
   if (H->d.staging) {
     OURO_DISPATCH(H->d.variant, (k_round_fused<V, true><<<grid_for(n, block, occupancy_grid(k_round_fused<V, true>, block)),
-                                                         block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs)));
+                                                         block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs,
+                                                                                work)));
   } else {
     OURO_DISPATCH(H->d.variant, (k_round_fused<V, false><<<grid_for(n, block, occupancy_grid(k_round_fused<V, false>, block)),
-                                                          block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs)));
+                                                          block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs,
+                                                                                 work)));
   }
   OURO_LAUNCHED();
   return OURO_OK;
