@@ -76,8 +76,8 @@ def dist_env():
 # from the sources whose digest is recorded; null once they change.
 FUSED_KERNEL_SOURCES = ("include/ouro_device.cuh", "paper_2504_18211_gb300/csrc/ouro_payload.cuh",
                         "paper_2504_18211_gb300/csrc/ouro_kernels.cu", "paper_2504_18211_gb300/csrc/ouro_internal.cuh")
-FUSED_TRAFFIC = {"sources_sha256": "064c9761870b3d143e29ee556293acb3e20cf9d1332a9f1839f1aca34fff759a",
-                 "bytes_per_launch": 1627118080}
+FUSED_TRAFFIC = {"sources_sha256": "25c47d941b099e8d0537e384700b0714e513d727c85ceee51ec0f71958f4a58d",
+                 "bytes_per_launch": 1632661760}
 
 
 def kernel_sources_digest() -> str:
