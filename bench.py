@@ -602,6 +602,21 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
                          "per_launch_ms": {k: round(x, 4) for k, x in pl2.items()}, "verified": ok}
     ex["variants"] = others
 
+    # ---- the deoptimised form of Sec. 2: no warp aggregation, fences for sleeps
+    deopt = {}
+    for v in ("page_array", "page_varray", "chunk_array"):
+        with P.Heap(HEAP_BYTES, CHUNK, v, deopt=True) as h4:
+            o4 = torch.zeros(5, dtype=torch.int64, device="cuda")
+            for _ in range(3):
+                h4.round_fused(sizes, SEED, 1, out=o4)
+            fms = timed(torch, stream, lambda: h4.round_fused(sizes, SEED, 1, out=o4), 5)
+            pl4 = per_launch(h4, 4)
+            ok = P.check_to_dict(o4)["mismatches"] == 0 and h4.stats()["error_bits"] == 0
+            deopt[v] = {"fused_mops": round(2 * n / (fms / 1e3) / 1e6, 1),
+                        "alloc_free_mops": round(2 * n / ((pl4["malloc"] + pl4["free"]) / 1e3) / 1e6, 1),
+                        "per_launch_ms": {k: round(x, 4) for k, x in pl4.items()}, "verified": ok}
+    ex["deoptimised"] = deopt
+
     # ---- the headline round with the other staging setting
     with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=args.no_staging) as h3:
         o3 = torch.zeros(5, dtype=torch.int64, device="cuda")

@@ -88,6 +88,10 @@ typedef struct {
   uint32_t checked;               /* page queues: track live pages to detect double frees */
   uint32_t staging;               /* page queues: the library's fused / persistent kernels stage
                                      freed pages per warp in shared memory (ouro_block_ctx) */
+  uint32_t deopt;                 /* the "deoptimised" form of Sec. 2: no warp aggregation (every
+                                     request takes its own queue atomics) and a memory fence where
+                                     a waiting thread would __nanosleep; for comparison only */
+  uint32_t reserved;              /* must be 0 */
 } ouro_options;
 
 /* Device view of a heap, passed BY VALUE to kernels that call ouro_malloc /
@@ -99,7 +103,7 @@ typedef struct {
   unsigned int chunk_bytes, log2_chunk, n_classes, variant;
   unsigned int seg_cap, words_per_chunk;
   unsigned int spin_limit, backoff_min_ns, backoff_max_ns, max_carve;
-  unsigned int checked, staging;
+  unsigned int checked, staging, deopt, pad;
   void *qhdr;                          /* per-class queue headers */
   unsigned long long *cells;           /* array variants: every class ring, back to back */
   unsigned long long ring_off[OURO_MAX_CLASSES];

@@ -203,6 +203,22 @@ __device__ __forceinline__ int slot_d(unsigned long long v, unsigned long long p
   return (int)((unsigned)(v >> 32) - (unsigned)pos);
 }
 
+/* Lanes of mask that share key: one warp group takes one queue atomic for
+ * all its lanes (warp aggregation).  The deoptimised form (option deopt,
+ * Sec. 2) makes every lane its own group. */
+template <typename T>
+__device__ __forceinline__ unsigned warp_group(const ouro_heap_dev &h, unsigned mask, T key) {
+  if (h.deopt) return 1u << laneid();
+  return __match_any_sync(mask, key);
+}
+
+/* One step of a bounded wait: __nanosleep with the caller's backoff, or in
+ * the deoptimised form a memory fence in its place (Sec. 2). */
+__device__ __forceinline__ void backoff_wait(const ouro_heap_dev &h, unsigned ns) {
+  if (h.deopt) __threadfence();
+  else __nanosleep(ns);
+}
+
 __device__ __forceinline__ bool try_lock(unsigned long long *l) {
   if (ld_rlx(l) != 0) return false;
   return cas_ar(l, 0ull, 1ull) == 0ull;
@@ -464,7 +480,7 @@ __device__ inline unsigned long long *va_slot(const ouro_heap_dev &h, int c, uns
       continue;
     }
     /* being created, or the entry still serves segment s - D (wait for it to retire) */
-    __nanosleep(ns);
+    backoff_wait(h, ns);
     ns = min(ns * 2, h.backoff_max_ns);
   }
   set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_VA_WAIT);
@@ -491,7 +507,7 @@ __device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsig
                                       unsigned mask) {
   const bool on = active && cell;
   const unsigned x = on ? (unsigned)(((const unsigned char *)cell - h.base) >> h.log2_chunk) : OURO_NIL;
-  const unsigned g = __match_any_sync(mask, x) & __ballot_sync(mask, on);
+  const unsigned g = warp_group(h, mask, x) & __ballot_sync(mask, on);
   if (on && laneid() == (unsigned)(__ffs(g) - 1)) {
     const unsigned n = __popc(g);
     const unsigned r = atomicAdd(&seg_of(h, x)->done, n) + n;
@@ -562,7 +578,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
         continue;
       }
       if (lo32(cur) == OURO_BUSY) {                  /* first segment being created */
-        __nanosleep(ns);
+        backoff_wait(h, ns);
         ns = min(ns * 2, h.backoff_max_ns);
         continue;
       }
@@ -600,7 +616,7 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
       continue;
     }
     if (nxt == OURO_BUSY) {                          /* someone is creating the successor */
-      __nanosleep(ns);
+      backoff_wait(h, ns);
       ns = min(ns * 2, h.backoff_max_ns);
       continue;
     }
@@ -660,7 +676,7 @@ __device__ inline int put_at(const ouro_heap_dev &h, unsigned long long *cell, u
     int d = slot_d(old, pos);
     if (d == 0 || (single_use && d < 0)) { expect = old; continue; }   /* empty (posted value / stale lap) */
     if (d >= 3) return 1;
-    __nanosleep(ns);
+    backoff_wait(h, ns);
     ns = min(ns * 2, h.backoff_max_ns);
     expect = slot(pos, 0);
   }
@@ -855,7 +871,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   const bool req = cls >= 0;
   ouro_qhdr *q = qh(h, req ? cls : 0);
   const unsigned lane = laneid();
-  const unsigned grp = __match_any_sync(vmask, cls);
+  const unsigned grp = warp_group(h, vmask, cls);
   const unsigned leader = __ffs(grp) - 1;
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long pos = 0;
@@ -915,7 +931,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
         break;
       }
       if (!__any_sync(vmask, progressed)) {
-        __nanosleep(ns);
+        backoff_wait(h, ns);
         ns = min(ns * 2, h.backoff_max_ns);
       } else {
         ns = h.backoff_min_ns;
@@ -936,7 +952,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
     res = h.base + ((size_t)item << (4 + cls));
   }
   /* per-class counters, one update per class group of the warp */
-  const unsigned g2 = __match_any_sync(vmask, cls);
+  const unsigned g2 = warp_group(h, vmask, cls);
   const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
   if (req && lane == (unsigned)(__ffs(g2) - 1)) {
     stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
@@ -951,7 +967,7 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
   constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, cls);
   const unsigned lane = laneid();
-  const unsigned grp = __match_any_sync(vmask, cls);
+  const unsigned grp = warp_group(h, vmask, cls);
   const unsigned leader = __ffs(grp) - 1;
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long t = 0;
@@ -1201,7 +1217,7 @@ __device__ inline unsigned claim_pages(const ouro_heap_dev &h, unsigned x, unsig
       if (!v) {
         w = (w + 1 == words_c) ? 0 : w + 1;
         if (++empty > words_c) {            /* a whole pass found nothing: bits still being freed */
-          __nanosleep(ns);
+          backoff_wait(h, ns);
           ns = min(ns * 2, h.backoff_max_ns);
           empty = 0;
         }
@@ -1243,7 +1259,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   for (unsigned it = 0;; ++it) {
     const unsigned pend = __ballot_sync(vmask, st == 0);
     if (!pend) break;
-    const unsigned gmask = __match_any_sync(vmask, st == 0 ? cls : -1) & pend;
+    const unsigned gmask = warp_group(h, vmask, st == 0 ? cls : -1) & pend;
     const bool mine = st == 0;
     const unsigned leader = mine ? __ffs(gmask) - 1 : 0;
     const unsigned rank = mine ? __popc(gmask & lanemask_lt()) : 0;
@@ -1361,7 +1377,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
     }
     if (__ballot_sync(vmask, st == 0) == 0) break;
     if (!any) {
-      __nanosleep(ns);
+      backoff_wait(h, ns);
       ns = min(ns * 2, h.backoff_max_ns);
     } else {
       ns = h.backoff_min_ns;
@@ -1369,7 +1385,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   }
   void *ret = nullptr;
   if (st == 1) ret = h.base + ((size_t)chunk << h.log2_chunk) + ((size_t)page << (4 + cls));
-  const unsigned g2 = __match_any_sync(vmask, cls);
+  const unsigned g2 = warp_group(h, vmask, cls);
   const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
   if (req && lane == (unsigned)(__ffs(g2) - 1)) {
     stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
@@ -1393,7 +1409,7 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
   /* 1. set the page bits, one atomicOr per (chunk, word) group */
   __threadfence();
   const unsigned long long wkey = cls >= 0 ? (((unsigned long long)x << 32) | (pg >> 5)) : ~0ull;
-  const unsigned wg = __match_any_sync(mask, wkey);
+  const unsigned wg = warp_group(h, mask, wkey);
   const unsigned bit = cls >= 0 ? 1u << (pg & 31) : 0u;
   const unsigned bits = __reduce_or_sync(wg, bit);
   unsigned old = 0;
@@ -1405,14 +1421,14 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
     cls = -1;
   }
   /* 2. count the pages back per chunk; lifting the count from <= 0 queues it */
-  const unsigned cg = __match_any_sync(mask, cls >= 0 ? x : OURO_NIL) & __ballot_sync(mask, cls >= 0);
+  const unsigned cg = warp_group(h, mask, cls >= 0 ? x : OURO_NIL) & __ballot_sync(mask, cls >= 0);
   if (cls >= 0 && lane == (unsigned)(__ffs(cg) - 1)) {
     const int k = __popc(cg);
     __threadfence();
     const int b = atomicAdd(&h.chunk_free[x], k);
     if (b <= 0 && b + k >= 1) chunk_push<QF>(h, cls, x);
   }
-  const unsigned sg = __match_any_sync(mask, cls);
+  const unsigned sg = warp_group(h, mask, cls);
   if (cls >= 0 && lane == (unsigned)(__ffs(sg) - 1)) stat_add(h, cls, OURO_ST_FREE, __popc(sg));
 }
 

@@ -21,11 +21,12 @@ class Heap:
 
     def __init__(self, bytes_: int, chunk_bytes: int, variant="page_array", *, spin_limit: int = 0,
                  backoff_min_ns: int = 0, backoff_max_ns: int = 0, max_carve: int = 0,
-                 array_queue_capacity: int = 0, checked: bool = False, staging: bool = False, heap_buf=None):
+                 array_queue_capacity: int = 0, checked: bool = False, staging: bool = False,
+                 deopt: bool = False, heap_buf=None):
         if isinstance(variant, str):
             variant = VARIANTS[variant]
         opt = Options(spin_limit, backoff_min_ns, backoff_max_ns, max_carve, array_queue_capacity,
-                      1 if checked else 0, 1 if staging else 0)
+                      1 if checked else 0, 1 if staging else 0, 1 if deopt else 0, 0)
         self._buf = heap_buf       # keep a caller buffer alive as long as the heap
         self.h = ouro_heap_create_ex(bytes_, chunk_bytes, variant, opt,
                                      heap_buf.data_ptr() if heap_buf is not None else 0)

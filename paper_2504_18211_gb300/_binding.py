@@ -32,7 +32,7 @@ class Options(C.Structure):
     _fields_ = [("spin_limit", C.c_uint32), ("backoff_min_ns", C.c_uint32),
                 ("backoff_max_ns", C.c_uint32), ("max_carve", C.c_uint32),
                 ("array_queue_capacity", C.c_uint64), ("checked", C.c_uint32),
-                ("staging", C.c_uint32)]
+                ("staging", C.c_uint32), ("deopt", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class HeapDev(C.Structure):
@@ -41,6 +41,7 @@ class HeapDev(C.Structure):
                 ("variant", C.c_uint), ("seg_cap", C.c_uint), ("words_per_chunk", C.c_uint),
                 ("spin_limit", C.c_uint), ("backoff_min_ns", C.c_uint), ("backoff_max_ns", C.c_uint),
                 ("max_carve", C.c_uint), ("checked", C.c_uint), ("staging", C.c_uint),
+                ("deopt", C.c_uint), ("pad", C.c_uint),
                 ("qhdr", C.c_void_p), ("cells", C.c_void_p),
                 ("ring_off", C.c_ulonglong * MAX_CLASSES), ("ring_mask", C.c_ulonglong * MAX_CLASSES),
                 ("qcap", C.c_ulonglong * MAX_CLASSES), ("chunk_cls", C.c_void_p),

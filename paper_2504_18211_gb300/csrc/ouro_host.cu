@@ -129,6 +129,8 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   o.array_queue_capacity = 1ull << 23;
   o.checked = 0;
   o.staging = 0;
+  o.deopt = 0;
+  o.reserved = 0;
   if (opt) {
     if (opt->spin_limit) o.spin_limit = opt->spin_limit;
     if (opt->backoff_min_ns) o.backoff_min_ns = opt->backoff_min_ns;
@@ -137,6 +139,8 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
     if (opt->array_queue_capacity) o.array_queue_capacity = opt->array_queue_capacity;
     o.checked = opt->checked;
     o.staging = opt->staging;
+    o.deopt = opt->deopt;
+    if (opt->reserved) return OURO_EINVAL;
   }
   if (o.backoff_max_ns < o.backoff_min_ns) o.backoff_max_ns = o.backoff_min_ns;
 
@@ -160,6 +164,8 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   d.max_carve = o.max_carve;
   d.checked = o.checked ? 1u : 0u;
   d.staging = (o.staging && is_page(variant)) ? 1u : 0u;
+  d.deopt = o.deopt ? 1u : 0u;
+  d.pad = 0;
 
   /* ring sizes (plain arrays); directory sizes (virtualized arrays): a
    * directory spans every position that can be live at once -- all items

@@ -297,3 +297,32 @@ def test_full_scale_sweep(ouro, variant):
         assert st2["error_bits"] == 0, (st2["error_bits"], st2["error_site"])
         heap.trim()
         same_canonical_as_post_create(heap.snapshot(), bytes_ // chunk)
+
+
+@pytest.mark.parametrize("variant", ALL_VARIANTS)
+def test_deoptimised_form(ouro, variant):
+    """The deoptimised form of Sec. 2 (no warp aggregation, a fence in place
+    of __nanosleep): per-launch and fused rounds give the oracle's counts and
+    checksums, page queues carve exactly, and free-all + trim restores the
+    post-create state."""
+    torch = torch_cuda()
+    threads = 16384 + 77
+    sizes = W.sweep_sizes(threads, seed=W.SEED_BASE + 13)
+    seed = 0xDE0F7
+    bytes_, chunk = 256 << 20, 8192
+    oh, ores = oracle_round(bytes_, chunk, variant, sizes, seed, 1, with_memory=True)
+    with ouro.Heap(bytes_, chunk, variant, deopt=True) as heap:
+        ptrs, chk, st_m, st = per_launch_round(ouro, heap, sizes, seed, 1)
+        assert chk == ores
+        assert_no_overlap(ptrs, sizes, heap.base, bytes_, chunk)
+        ost = oh.stats()
+        assert st["mallocs"] == ost["mallocs"] and st["frees"] == ost["frees"]
+        assert carve_bounds_ok(variant, st_m["carves"], ost["carves"], sizes, chunk), (st_m["carves"], ost["carves"])
+        for _ in range(2):
+            out = heap.round_fused(to_dev(sizes), seed, 1)
+            assert ouro.check_to_dict(out) == ores
+        torch.cuda.synchronize()
+        st = heap.stats()
+        assert st["error_bits"] == 0 and sum(st["live"]) == 0
+        heap.trim()
+        same_canonical_as_post_create(heap.snapshot(), bytes_ // chunk)
