@@ -617,6 +617,24 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
                         "per_launch_ms": {k: round(x, 4) for k, x in pl4.items()}, "verified": ok}
     ex["deoptimised"] = deopt
 
+    # ---- CUDA's built-in device malloc on the same round (the baseline of Sec. 1)
+    try:
+        got = P.ouro_cuda_malloc_heap(HEAP_BYTES)
+        o5 = torch.zeros(5, dtype=torch.int64, device="cuda")
+        t0 = time.perf_counter()
+        P.ouro_cuda_malloc_round(sizes, SEED, 1, out=o5)
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t0
+        reps = 3 if first_s < 2.0 else 0
+        cms = timed(torch, stream, lambda: P.ouro_cuda_malloc_round(sizes, SEED, 1, out=o5), reps) if reps else first_s * 1e3
+        c5 = P.check_to_dict(o5)
+        ex["cuda_device_malloc"] = {"fused_mops": round(2 * n / (cms / 1e3) / 1e6, 1), "ms": round(cms, 3),
+                                    "first_round_s": round(first_s, 3), "nulls": c5["nulls"],
+                                    "mismatches": c5["mismatches"], "heap_bytes": got,
+                                    "timed_rounds": reps}
+    except P.OuroError as e:
+        ex["cuda_device_malloc"] = {"unavailable": str(e)}
+
     # ---- the headline round with the other staging setting
     with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=args.no_staging) as h3:
         o3 = torch.zeros(5, dtype=torch.int64, device="cuda")

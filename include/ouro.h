@@ -341,6 +341,19 @@ ouro_status ouro_probe_atomics(unsigned long long *d_buf, size_t words, int patt
 ouro_status ouro_malloc_latency(ouro_heap *h, const uint32_t *d_sizes, void **d_ptrs, size_t n,
                                 unsigned long long *d_hist, void *stream);
 
+/* ---- comparison: CUDA's built-in device malloc (Sec. 1) -------------------- */
+/* Size the current context's device-malloc heap (cudaLimitMallocHeapSize;
+ * it lasts as long as the context).  Must precede the first launch of any
+ * kernel that calls malloc in this context: CUDA fixes the heap then, after
+ * which the call returns OURO_ECUDA.  *got_bytes (host, optional): the size
+ * CUDA reports back. */
+ouro_status ouro_cuda_malloc_heap(size_t bytes, size_t *got_bytes);
+/* The driver round of ouro_round_fused with CUDA's device malloc / free in
+ * place of this library's heap: every request mallocs its size, writes its
+ * pattern, reads it back and frees.  *d_out (device) receives the check. */
+ouro_status ouro_cuda_malloc_round(const uint32_t *d_sizes, size_t n, uint32_t seed, int mode,
+                                   ouro_check *d_out, void *stream);
+
 /* ---- misc ----------------------------------------------------------------- */
 const char *ouro_status_string(ouro_status s);
 int ouro_last_cuda_error(void);

@@ -12,6 +12,7 @@ from ._binding import (CHUNK_ARRAY, CHUNK_VARRAY, CHUNK_VLIST, PAGE_ARRAY, PAGE_
                        OuroError, check_to_dict, load, ouro_batch_free, ouro_batch_malloc,
                        ouro_debug_stall_producer, ouro_heap_create_ex, ouro_heap_destroy,
                        ouro_heap_device, ouro_heap_reset, ouro_heap_snapshot, ouro_heap_stats,
+                       ouro_cuda_malloc_heap, ouro_cuda_malloc_round,
                        ouro_heap_trim, ouro_kernel_launches, ouro_malloc_latency, ouro_pattern_check,
                        ouro_pattern_write, ouro_probe_atomics, ouro_round_fused, ouro_status_string)
 

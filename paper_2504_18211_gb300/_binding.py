@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "ouro_debug_stall_producer": (st, [vp, i32, u32, vp]),
         "ouro_probe_atomics": (st, [vp, sz, i32, u32, i32, vp]),
         "ouro_malloc_latency": (st, [vp, vp, vp, sz, vp, vp]),
+        "ouro_cuda_malloc_heap": (st, [sz, C.POINTER(sz)]),
+        "ouro_cuda_malloc_round": (st, [vp, sz, u32, i32, vp, vp]),
         "ouro_heap_stats_static": (st, [vp, C.POINTER(Stats), vp]),
         "ouro_batches_persistent": (st, [vp, vp, vp, vp, u32, u64, u32, i32, vp, vp, i32, vp]),
         "ouro_batch_graph_create": (st, [vp, vp, vp, u32, u32, i32, vp, vp, i32, C.POINTER(vp)]),
@@ -273,6 +275,23 @@ def ouro_probe_atomics(buf, pattern: int, iters: int, blocks: int, stream=None) 
 def ouro_malloc_latency(h: int, sizes, ptrs, hist, stream=None) -> None:
     _check("ouro_malloc_latency", load().ouro_malloc_latency(C.c_void_p(h), _ptr(sizes), _ptr(ptrs),
                                                               sizes.numel(), _ptr(hist), _stream(stream)))
+
+
+def ouro_cuda_malloc_heap(nbytes: int) -> int:
+    """Size CUDA's device-malloc heap of this context; returns the size CUDA reports."""
+    got = C.c_size_t(0)
+    _check("ouro_cuda_malloc_heap", load().ouro_cuda_malloc_heap(nbytes, C.byref(got)))
+    return got.value
+
+
+def ouro_cuda_malloc_round(sizes, seed: int, mode: int = 1, out=None, stream=None):
+    """The fused driver round on CUDA's device malloc / free; returns the check tensor."""
+    import torch
+    if out is None:
+        out = torch.zeros(5, dtype=torch.int64, device=sizes.device)
+    _check("ouro_cuda_malloc_round", load().ouro_cuda_malloc_round(_ptr(sizes), sizes.numel(), seed & 0xFFFFFFFF,
+                                                                    mode, _ptr(out), _stream(stream)))
+    return out
 
 
 def latency_bin_bounds(b: int):

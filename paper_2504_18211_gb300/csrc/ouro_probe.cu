@@ -70,6 +70,27 @@ __global__ void k_malloc_timed(ouro_heap_dev h, const uint32_t *sizes, void **pt
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
+/* The fused driver round on CUDA's built-in device allocator: the same
+ * warp payload, with malloc / free of the CUDA runtime. */
+__global__ void __launch_bounds__(256) k_cuda_malloc_round(const uint32_t *sizes, size_t n, uint32_t seed,
+                                                           int mode, ouro_check *out) {
+  payload_acc a;
+  unsigned long long nulls = 0;
+  const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  const size_t wid = (((size_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5;
+  for (size_t base = wid * 32; base < n; base += warps * 32) {
+    const size_t i = base + (threadIdx.x & 31);
+    const uint32_t sz = i < n ? sizes[i] : 0;
+    unsigned char *p = i < n ? static_cast<unsigned char *>(malloc(sz)) : nullptr;
+    if (i < n && !p) nulls++;
+    __syncwarp();
+    warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed, mode, a);
+    __syncwarp();
+    if (p) free(p);
+  }
+  flush_acc(a, nulls, out);
+}
+
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
@@ -78,6 +99,32 @@ extern "C" ouro_status ouro_probe_atomics(unsigned long long *d_buf, size_t word
                                           int blocks, void *stream) {
   if (!d_buf || words < 32 * 16 || pattern < 0 || pattern > 2 || blocks <= 0) return OURO_EINVAL;
   k_probe<<<blocks, 256, 0, S(stream)>>>(d_buf, words, pattern, iters, d_buf + words - 1);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_cuda_malloc_heap(size_t bytes, size_t *got_bytes) {
+  if (!bytes) return OURO_EINVAL;
+  OURO_CUDA(cudaDeviceSetLimit(cudaLimitMallocHeapSize, bytes));
+  size_t got = 0;
+  OURO_CUDA(cudaDeviceGetLimit(&got, cudaLimitMallocHeapSize));
+  if (got_bytes) *got_bytes = got;
+  return OURO_OK;
+}
+
+extern "C" ouro_status ouro_cuda_malloc_round(const uint32_t *d_sizes, size_t n, uint32_t seed, int mode,
+                                              ouro_check *d_out, void *stream) {
+  if (!d_out || (n && !d_sizes)) return OURO_EINVAL;
+  if (mode != 0 && mode != 1) return OURO_EINVAL;
+  OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check), S(stream)));
+  if (!n) return OURO_OK;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cuda_malloc_round, 256, 0);
+  if (per_sm < 1) per_sm = 1;
+  size_t g = (n + 255) / 256;
+  const size_t cap = (size_t)per_sm * ouro::host::sm_count();
+  if (g > cap) g = cap;
+  k_cuda_malloc_round<<<(int)g, 256, 0, S(stream)>>>(d_sizes, n, seed, mode, d_out);
   OURO_LAUNCHED();
   return OURO_OK;
 }
