@@ -127,11 +127,12 @@ typedef struct {
   uint64_t live[OURO_MAX_CLASSES];        /* mallocs - frees */
   uint64_t repushes[OURO_MAX_CLASSES];    /* items re-queued after a consumer gave up a slot */
   uint64_t dead[OURO_MAX_CLASSES];        /* queue positions answered with null (heap exhausted) */
-  uint64_t zero_reqs, too_large;          /* requests of 0 bytes / above one chunk */
+  uint64_t zero_reqs, too_large;          /* requests of 0 bytes / above 1 MiB */
   uint64_t bump, pool_size, seg_chunks, spare_chunks;
-  uint32_t error_bits, n_classes;
+  uint32_t error_bits, n_classes;         /* n_classes: classes that fit in one chunk */
   uint32_t error_site;                    /* where the first error was recorded (device header's OURO_SITE_*) */
-  uint32_t reserved;
+  uint32_t n_large;                       /* classes above one chunk: entries n_classes .. n_classes+n_large-1
+                                             of the per-class arrays; queued = free runs of the class */
 } ouro_stats;
 
 /* Host copy of the queue state, for tests (ouro_heap_snapshot).  Arrays are
@@ -147,6 +148,16 @@ typedef struct {
   uint64_t queue_n[OURO_MAX_CLASSES];
   uint32_t *queue[OURO_MAX_CLASSES];     /* items from head to tail, null answers skipped */
 } ouro_snapshot;
+
+/* ---- size classes --------------------------------------------------------
+ * A request of n bytes (1 <= n <= 1 MiB) has class c = max(0, ceil(log2 n) - 4),
+ * i.e. 16 << c bytes (Sec. 4.2: queues of power-of-two sizes).  Classes that
+ * fit in one chunk (c < n_classes = log2(chunk_bytes) - 3) are pages of chunks
+ * served by the class queues.  Larger classes (the paper is silent on them)
+ * are runs of 2^(c - n_classes + 1) contiguous chunks: a freed run waits on
+ * its class's stack for reuse; a new run is cut at the bump pointer (pooled
+ * chunks are not gathered into runs); ouro_heap_trim returns free runs to the
+ * pool.  0 bytes and more than 1 MiB: null, counted. */
 
 /* ---- heap life cycle (Sec. 1: the host preallocates the heap) ---------- */
 

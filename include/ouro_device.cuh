@@ -43,6 +43,10 @@
 #define OURO_BUSY 0xFFFFFFFEu   /* successor segment being created by one thread */
 #define OURO_CLS_NONE 0xFFu
 #define OURO_CLS_SEG 0xFEu
+#define OURO_CLS_RUN_FREE 0x40u   /* | class: first chunk of a free run (on its class stack) */
+#define OURO_CLS_RUN_BODY 0x80u   /* | class: second or later chunk of a run */
+#define OURO_MAX_REQUEST (16ull << (OURO_MAX_CLASSES - 1))   /* 1 MiB */
+#define OURO_ROW_NONE OURO_MAX_CLASSES   /* counter row of requests without a class */
 #define OURO_VL_HINTS 1024
 #define OURO_NSTAT 8
 #define OURO_SHARDS 32
@@ -92,6 +96,8 @@ struct ouro_glob {
   unsigned long long pool_size;
   unsigned int error_bits;
   unsigned int error_site;   /* OURO_SITE_* of the first error */
+  ouro_line run_top[OURO_MAX_CLASSES];   /* classes above one chunk: free-run stack,
+                                            (tag << 32) | (first chunk + 1), 0 = empty */
 };
 
 /* header of a virtualized-list segment (first 64 bytes of its chunk) */
@@ -179,16 +185,18 @@ enum {
   OURO_SITE_SPARE = 1, OURO_SITE_VL_FIRST, OURO_SITE_VL_NEXT, OURO_SITE_VL_WALK, OURO_SITE_PUT,
   OURO_SITE_PUSH_ONE, OURO_SITE_PAGE_GIVEUP, OURO_SITE_PAGE_CHECKED, OURO_SITE_CLAIM,
   OURO_SITE_CHUNK_GIVEUP, OURO_SITE_CHUNK_DOUBLE, OURO_SITE_BAD_FREE, OURO_SITE_PAGE_DOUBLE,
-  OURO_SITE_TRIM, OURO_SITE_GRAPH_LOCK, OURO_SITE_VA_NEW, OURO_SITE_VA_WAIT
+  OURO_SITE_TRIM, OURO_SITE_GRAPH_LOCK, OURO_SITE_VA_NEW, OURO_SITE_VA_WAIT, OURO_SITE_RUN_FREE
 };
 __device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits, unsigned site) {
   atomicOr(&gl(h)->error_bits, bits);
   atomicCAS(&gl(h)->error_site, 0u, site);
 }
 
-/* power-of-two class: ceil(log2 n) - 4, floor 16 B; -1 for 0 or above one chunk */
+/* power-of-two class: ceil(log2 n) - 4, floor 16 B; -1 for 0 or above
+ * 1 MiB.  Classes from h.n_classes up are runs of chunks. */
 __device__ __forceinline__ int size_class(const ouro_heap_dev &h, unsigned long long n) {
-  if (n == 0 || n > h.chunk_bytes) return -1;
+  (void)h;
+  if (n == 0 || n > OURO_MAX_REQUEST) return -1;
   if (n <= 16) return 0;
   return 64 - __clzll(n - 1) - 4;
 }
@@ -994,16 +1002,98 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
   }
 }
 
-/* Locate a block: class and page id, or -1 after recording a bad free. */
+/* Locate a block: class and page id (a class of one chunk or less), or
+ * class and first chunk (a run); -1 when p is no block start. */
 __device__ __forceinline__ int locate(const ouro_heap_dev &h, const void *p, unsigned *item) {
   const unsigned char *b = static_cast<const unsigned char *>(p);
   if (b < h.base || b >= h.base + h.bytes) return -1;
   const unsigned long long off = (unsigned long long)(b - h.base);
-  const unsigned c = h.chunk_cls[off >> h.log2_chunk];
-  if (c >= h.n_classes) return -1;
-  if (off & ((16ull << c) - 1)) return -1;
-  *item = (unsigned)(off >> (4 + c));
+  unsigned c = h.chunk_cls[off >> h.log2_chunk];
+  if (c < h.n_classes) {
+    if (off & ((16ull << c) - 1)) return -1;
+    *item = (unsigned)(off >> (4 + c));
+    return (int)c;
+  }
+  if ((c & 0xC0u) == OURO_CLS_RUN_FREE) c &= 0x3Fu;   /* a free run: run_free reports the double free */
+  if (c >= OURO_MAX_CLASSES || (off & (h.chunk_bytes - 1))) return -1;
+  *item = (unsigned)(off >> h.log2_chunk);
   return (int)c;
+}
+
+/* ------------------------------------------------ runs above one chunk */
+/* Requests above one chunk (the paper is silent on them): class c >=
+ * n_classes is a run of 2^(c - n_classes + 1) contiguous chunks.  Freed runs
+ * wait on a per-class stack (tagged; the link lives in the run's first
+ * word); a new run is cut at the bump pointer by compare-and-swap, so it is
+ * contiguous and never runs past the heap.  One lane per request: large
+ * requests are few and each moves many bytes. */
+__device__ inline void *run_malloc(const ouro_heap_dev &h, int c) {
+  ouro_glob *g = gl(h);
+  unsigned long long *top = &g->run_top[c].v;
+  const unsigned long long k = 1ull << (c - (int)h.n_classes + 1);
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    const unsigned long long old = ld_acq(top);
+    if (!lo32(old)) break;
+    const unsigned x = lo32(old) - 1;
+    const unsigned nxt = *(volatile unsigned *)(h.base + ((size_t)x << h.log2_chunk));
+    if (cas_ar(top, old, pack(hi32(old) + 1, nxt)) == old) {
+      h.chunk_cls[x] = (unsigned char)c;                 /* live again */
+      __threadfence();
+      stat_add(h, c, OURO_ST_MALLOC, 1);
+      return h.base + ((size_t)x << h.log2_chunk);
+    }
+  }
+  unsigned long long b = ld_rlx(&g->bump.v);
+  for (unsigned it = 0; it < h.spin_limit && b + k <= h.n_chunks; ++it) {
+    const unsigned long long seen = atomicCAS(&g->bump.v, b, b + k);
+    if (seen == b) {
+      for (unsigned long long i = 1; i < k; ++i) h.chunk_cls[b + i] = (unsigned char)(OURO_CLS_RUN_BODY | c);
+      h.chunk_cls[b] = (unsigned char)c;
+      __threadfence();
+      stat_add(h, c, OURO_ST_MALLOC, 1);
+      stat_add(h, c, OURO_ST_CARVE, k);
+      return h.base + ((size_t)b << h.log2_chunk);
+    }
+    b = seen;
+  }
+  stat_add(h, c, OURO_ST_FAILED, 1);
+  return nullptr;
+}
+
+/* Free the run of class c starting at chunk x: its class byte turns from
+ * c to RUN_FREE | c in one compare-and-swap of the word holding it (so a
+ * second free of the same run is seen), then the run goes on the stack. */
+__device__ inline void run_free(const ouro_heap_dev &h, int c, unsigned x) {
+  unsigned *w = reinterpret_cast<unsigned *>(h.chunk_cls + (x & ~3u));
+  const unsigned sh = (x & 3u) * 8u;
+  bool ok = false;
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    const unsigned v = *(volatile unsigned *)w;
+    const unsigned byte = (v >> sh) & 0xFFu;
+    if (byte != (unsigned)c) {
+      set_error(h, byte == (OURO_CLS_RUN_FREE | (unsigned)c) ? OURO_ERR_DOUBLE_FREE : OURO_ERR_BAD_FREE,
+                OURO_SITE_RUN_FREE);
+      return;
+    }
+    if (atomicCAS(w, v, (v & ~(0xFFu << sh)) | ((OURO_CLS_RUN_FREE | (unsigned)c) << sh)) == v) {
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) {
+    set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_RUN_FREE);
+    return;
+  }
+  stat_add(h, c, OURO_ST_FREE, 1);
+  unsigned long long *top = &gl(h)->run_top[c].v;
+  volatile unsigned *link = reinterpret_cast<volatile unsigned *>(h.base + ((size_t)x << h.log2_chunk));
+  for (unsigned it = 0; it < h.spin_limit; ++it) {
+    const unsigned long long old = ld_acq(top);
+    *link = lo32(old);
+    __threadfence();
+    if (cas_ar(top, old, pack(hi32(old) + 1, x + 1)) == old) return;
+  }
+  set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_RUN_FREE);
 }
 
 /* ------------------------------------------------------- chunk queues */
@@ -1460,7 +1550,13 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
   const unsigned mask = __activemask();
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   int cls = want ? size_class(h, n) : -1;
-  if (want && cls < 0) stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+  if (want && cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+  void *run = nullptr;
+  const bool is_run = cls >= (int)h.n_classes;
+  if (is_run) {                       /* above one chunk: a run, then help the others */
+    run = run_malloc(h, cls);
+    cls = -1;
+  }
   const unsigned g = __match_any_sync(mask, cls);
   const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
   unsigned have = 0, take = 0;
@@ -1489,7 +1585,7 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
     void *p = page_malloc<V>(h, rest, mask);
     if (rest >= 0) res = p;
   }
-  return res;
+  return is_run ? run : res;
 }
 
 /* staged free for page queues; every lane of the warp's call mask calls */
@@ -1502,7 +1598,10 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
   if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
-    else if (h.checked) {
+    else if (cls >= (int)h.n_classes) {
+      run_free(h, cls, item);
+      cls = -1;
+    } else if (h.checked) {
       const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
       const unsigned bit = 1u << (pg & 31);
       __threadfence();
@@ -1568,24 +1667,32 @@ __device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev
 }
 
 /* ------------------------------------------------------------- public API */
-/* Allocate n bytes from the heap; null when n is 0 or above one chunk, when
+/* Allocate n bytes from the heap; null when n is 0 or above 1 MiB, when
  * the heap is exhausted, or when a bounded wait ran out. */
 static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t n) {
   using namespace ouro::detail;
   const unsigned mask = __activemask();
-  const int cls = size_class(h, n);
-  if (cls < 0) stat_add(h, h.n_classes, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
-  if (!__any_sync(mask, cls >= 0)) return nullptr;
-  /* lanes without a class stay in as helpers of the warp's carves */
-  switch (h.variant) {
-    case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, mask);
-    case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, mask);
-    case OURO_CHUNK_ARRAY: return chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, mask);
-    case OURO_CHUNK_VLIST: return chunk_malloc<OURO_CHUNK_VLIST>(h, cls, mask);
-    case OURO_PAGE_VARRAY: return page_malloc<OURO_PAGE_VARRAY>(h, cls, mask);
-    case OURO_CHUNK_VARRAY: return chunk_malloc<OURO_CHUNK_VARRAY>(h, cls, mask);
-    default: return nullptr;
+  int cls = size_class(h, n);
+  if (cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+  void *run = nullptr;
+  const bool is_run = cls >= (int)h.n_classes;
+  if (is_run) {                       /* above one chunk: a run of chunks */
+    run = run_malloc(h, cls);
+    cls = -1;
   }
+  if (!__any_sync(mask, cls >= 0)) return run;
+  /* lanes without a class stay in as helpers of the warp's carves */
+  void *r;
+  switch (h.variant) {
+    case OURO_PAGE_ARRAY: r = page_malloc<OURO_PAGE_ARRAY>(h, cls, mask); break;
+    case OURO_PAGE_VLIST: r = page_malloc<OURO_PAGE_VLIST>(h, cls, mask); break;
+    case OURO_CHUNK_ARRAY: r = chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, mask); break;
+    case OURO_CHUNK_VLIST: r = chunk_malloc<OURO_CHUNK_VLIST>(h, cls, mask); break;
+    case OURO_PAGE_VARRAY: r = page_malloc<OURO_PAGE_VARRAY>(h, cls, mask); break;
+    case OURO_CHUNK_VARRAY: r = chunk_malloc<OURO_CHUNK_VARRAY>(h, cls, mask); break;
+    default: r = nullptr;
+  }
+  return is_run ? run : r;
 }
 
 /* Return a block to the heap; null is ignored; a pointer that is not a live
@@ -1598,7 +1705,10 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
   if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
-    else if (h.checked && ouro_page_queues((int)h.variant)) {
+    else if (cls >= (int)h.n_classes) {   /* a run */
+      run_free(h, cls, item);
+      cls = -1;
+    } else if (h.checked && ouro_page_queues((int)h.variant)) {
       unsigned ppcm = (1u << (h.log2_chunk - 4 - cls)) - 1;
       unsigned pg = item & ppcm, x = item >> (h.log2_chunk - 4 - cls);
       unsigned bit = 1u << (pg & 31);

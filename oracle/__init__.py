@@ -56,7 +56,8 @@ class _Stats(C.Structure):
                 ("zero_reqs", C.c_uint64), ("too_large", C.c_uint64),
                 ("bump", C.c_uint64), ("pool_size", C.c_uint64),
                 ("seg_chunks", C.c_uint64), ("spare_chunks", C.c_uint64),
-                ("error_bits", C.c_uint32), ("n_classes", C.c_uint32)]
+                ("error_bits", C.c_uint32), ("n_classes", C.c_uint32),
+                ("n_large", C.c_uint32), ("pad", C.c_uint32)]
 
 
 class RoundResult(C.Structure):
@@ -155,7 +156,7 @@ class OracleHeap:
     def stats(self) -> dict:
         s = _Stats()
         self.lib.orc_get_stats(self.h, C.byref(s))
-        nc = self.n_classes
+        nc = s.n_classes + s.n_large            # classes within one chunk, then runs of chunks
         out = {k: [int(x) for x in getattr(s, k)[:nc]]
                for k in ("mallocs", "frees", "failed", "carves", "carved_now", "queued", "live")}
         for k in ("zero_reqs", "too_large", "bump", "pool_size", "seg_chunks",
@@ -194,7 +195,7 @@ class OracleHeap:
     def canonical_state(self) -> dict:
         """Schedule-independent view of the queues: sorted items per class,
         sorted pool, bump pointer and the chunk class table."""
-        return {"queues": [np.sort(self.queue_items(c)) for c in range(self.n_classes)],
+        return {"queues": [np.sort(self.queue_items(c)) for c in range(MAX_CLASSES)],
                 "pool": np.sort(self.pool_items()), "bump": self.stats()["bump"],
                 "chunk_cls": self.chunk_classes()}
 

@@ -13,6 +13,9 @@
 
 #define CLS_NONE (-1)   /* chunk never carved, or back in the pool */
 #define CLS_SEG  (-2)   /* chunk holds a segment of a virtualized queue */
+#define CLS_RUN_FREE 64   /* + class: first chunk of a free run (on its class stack) */
+#define CLS_RUN_BODY 128  /* + class: second or later chunk of a run */
+#define MAX_REQUEST (16ull << (ORC_MAX_CLASSES - 1))   /* 1 MiB */
 
 /* ------------------------------------------------------------------ FIFO */
 typedef struct { uint64_t *v; uint64_t cap, lo, n; } fifo;
@@ -59,6 +62,7 @@ struct orc_heap {
   fifo segs[ORC_MAX_CLASSES];
   uint64_t seg_first[ORC_MAX_CLASSES];
   fifo spare[ORC_MAX_CLASSES];
+  fifo runs[ORC_MAX_CLASSES];   /* classes above one chunk: free runs, used as a stack */
   uint64_t carved_now[ORC_MAX_CLASSES];
   uint64_t mallocs[ORC_MAX_CLASSES], frees[ORC_MAX_CLASSES], failed[ORC_MAX_CLASSES],
            carves[ORC_MAX_CLASSES];
@@ -86,14 +90,21 @@ static int varray(const orc_heap *h) {
 int orc_num_classes(uint64_t chunk_bytes) { return log2u(chunk_bytes) - 4 + 1; }
 uint64_t orc_page_bytes(int cls) { return 16ull << cls; }
 
-/* Smallest power of two >= max(n, 16); requests of 0 bytes or above one chunk
- * have no class and are answered with null (reading: the paper is silent). */
+int orc_num_large(uint64_t chunk_bytes) { return ORC_MAX_CLASSES - orc_num_classes(chunk_bytes); }
+
+/* Smallest power of two >= max(n, 16); requests of 0 bytes or above 1 MiB
+ * have no class and are answered with null (reading: the paper is silent).
+ * Classes above the chunk size are runs of contiguous chunks (reading). */
 int orc_size_class(uint64_t chunk_bytes, uint64_t n) {
-  if (n == 0 || n > chunk_bytes) return -1;
+  (void)chunk_bytes;
+  if (n == 0 || n > MAX_REQUEST) return -1;
   int c = 0;
   while (orc_page_bytes(c) < n) c++;
   return c;
 }
+
+/* chunks in one run of class c (c >= n_classes): the class size / chunk */
+static uint64_t run_chunks(const orc_heap *h, int c) { return orc_page_bytes(c) / h->chunk_bytes; }
 
 static uint64_t pages_per_chunk(const orc_heap *h, int c) {
   return h->chunk_bytes / orc_page_bytes(c);
@@ -141,7 +152,7 @@ orc_heap *orc_create(uint64_t bytes, uint64_t chunk_bytes, int variant, uint64_t
 void orc_destroy(orc_heap *h) {
   if (!h) return;
   for (int c = 0; c < ORC_MAX_CLASSES; c++) {
-    fifo_free(&h->q[c]); fifo_free(&h->segs[c]); fifo_free(&h->spare[c]);
+    fifo_free(&h->q[c]); fifo_free(&h->segs[c]); fifo_free(&h->spare[c]); fifo_free(&h->runs[c]);
   }
   fifo_free(&h->pool);
   free(h->chunk_cls); free(h->live); free(h->free_pages); free(h->bits);
@@ -155,7 +166,7 @@ void orc_reset(orc_heap *h) {
   if (h->free_pages) memset(h->free_pages, 0, h->n_chunks * sizeof(uint32_t));
   if (h->bits) memset(h->bits, 0, h->n_chunks * h->words_per_chunk * sizeof(uint64_t));
   for (int c = 0; c < ORC_MAX_CLASSES; c++) {
-    fifo_clear(&h->q[c]); fifo_clear(&h->segs[c]); fifo_clear(&h->spare[c]);
+    fifo_clear(&h->q[c]); fifo_clear(&h->segs[c]); fifo_clear(&h->spare[c]); fifo_clear(&h->runs[c]);
     h->qhead[c] = h->qtail[c] = h->seg_first[c] = 0;
     h->carved_now[c] = h->mallocs[c] = h->frees[c] = h->failed[c] = h->carves[c] = 0;
   }
@@ -251,11 +262,37 @@ static int carve(orc_heap *h, int c) {
   return 0;
 }
 
+/* ---------------------------------------------- runs above one chunk */
+/* A request above one chunk takes a run of run_chunks(c) contiguous chunks:
+ * the last freed run of its class first; else a run cut at the bump
+ * pointer, the only place where contiguous chunks are sure to be free
+ * (pooled chunks are not reused for runs).  Reading: the paper is silent
+ * on requests larger than a chunk. */
+static int64_t run_malloc(orc_heap *h, int c) {
+  uint64_t k = run_chunks(h, c), x;
+  if (h->runs[c].n) {
+    x = fifo_pop_back(&h->runs[c]);
+  } else {
+    if (h->bump + k > h->n_chunks) { h->failed[c]++; return -1; }
+    x = h->bump;
+    h->bump += k;
+    for (uint64_t i = 1; i < k; i++) h->chunk_cls[x + i] = (int16_t)(CLS_RUN_BODY + c);
+    h->carves[c] += k;
+    h->carved_now[c] += k;
+  }
+  h->chunk_cls[x] = (int16_t)c;
+  uint64_t off = x * h->chunk_bytes;
+  live_set(h, off, 1);
+  h->mallocs[c]++;
+  return (int64_t)off;
+}
+
 /* -------------------------------------------------------------- malloc */
 int64_t orc_malloc(orc_heap *h, uint64_t n) {
   if (n == 0) { h->zero_reqs++; return -1; }
   int c = orc_size_class(h->chunk_bytes, n);
   if (c < 0) { h->too_large++; return -1; }
+  if (c >= h->n_classes) return run_malloc(h, c);
   uint64_t pb = orc_page_bytes(c);
   uint64_t off;
   if (page_variant(h)) {
@@ -286,7 +323,17 @@ uint32_t orc_free(orc_heap *h, int64_t off_s) {
   uint64_t off = (uint64_t)off_s;
   uint64_t x = off / h->chunk_bytes;
   int c = h->chunk_cls[x];
-  if (c < 0) { h->err |= ORC_ERR_BAD_FREE; return ORC_ERR_BAD_FREE; }
+  if (c < 0 || c >= CLS_RUN_BODY) { h->err |= ORC_ERR_BAD_FREE; return ORC_ERR_BAD_FREE; }
+  if (c >= CLS_RUN_FREE || c >= h->n_classes) {
+    /* a run: only its first byte is a block start; a free run is a double free */
+    if (off % h->chunk_bytes) { h->err |= ORC_ERR_BAD_FREE; return ORC_ERR_BAD_FREE; }
+    if (c >= CLS_RUN_FREE) { h->err |= ORC_ERR_DOUBLE_FREE; return ORC_ERR_DOUBLE_FREE; }
+    live_set(h, off, 0);
+    h->frees[c]++;
+    h->chunk_cls[x] = (int16_t)(CLS_RUN_FREE + c);
+    fifo_push(&h->runs[c], x);
+    return 0;
+  }
   uint64_t pb = orc_page_bytes(c);
   if (off % pb) { h->err |= ORC_ERR_BAD_FREE; return ORC_ERR_BAD_FREE; }
   if (!live_get(h, off)) { h->err |= ORC_ERR_DOUBLE_FREE; return ORC_ERR_DOUBLE_FREE; }
@@ -322,7 +369,7 @@ void orc_trim(orc_heap *h) {
   }
   for (uint64_t x = 0; x < h->n_chunks; x++) {
     int c = h->chunk_cls[x];
-    if (c < 0) continue;
+    if (c < 0 || c >= h->n_classes) continue;   /* runs are handled below */
     uint64_t ppc = pages_per_chunk(h, c);
     uint64_t fr = page_variant(h) ? qcount[x] : h->free_pages[x];
     if (fr == ppc) reclaim[x] = 1;
@@ -354,6 +401,19 @@ void orc_trim(orc_heap *h) {
   if (!page_variant(h))
     for (uint64_t x = 0; x < h->n_chunks; x++)
       if (reclaim[x]) memset(h->bits + x * h->words_per_chunk, 0, h->words_per_chunk * 8);
+  /* 3b. every chunk of every free run goes back to the pool too */
+  for (int c = h->n_classes; c < ORC_MAX_CLASSES; c++) {
+    uint64_t k = run_chunks(h, c);
+    for (uint64_t i = 0; i < h->runs[c].n; i++) {
+      uint64_t x = fifo_at(&h->runs[c], i);
+      for (uint64_t j = 0; j < k; j++) {
+        h->chunk_cls[x + j] = CLS_NONE;
+        fifo_push(&h->pool, x + j);
+      }
+      h->carved_now[c] -= k;
+    }
+    fifo_clear(&h->runs[c]);
+  }
   /* 4. canonical pool: ascending ids; lower the bump pointer over pooled chunks */
   uint64_t np = h->pool.n;
   uint64_t *pv = (uint64_t *)malloc((np ? np : 1) * sizeof(uint64_t));
@@ -382,13 +442,14 @@ void orc_trim(orc_heap *h) {
 void orc_get_stats(const orc_heap *h, orc_stats *o) {
   memset(o, 0, sizeof(*o));
   o->n_classes = (uint32_t)h->n_classes;
-  for (int c = 0; c < h->n_classes; c++) {
+  o->n_large = (uint32_t)(ORC_MAX_CLASSES - h->n_classes);
+  for (int c = 0; c < ORC_MAX_CLASSES; c++) {
     o->mallocs[c] = h->mallocs[c];
     o->frees[c] = h->frees[c];
     o->failed[c] = h->failed[c];
     o->carves[c] = h->carves[c];
     o->carved_now[c] = h->carved_now[c];
-    o->queued[c] = h->q[c].n;
+    o->queued[c] = c < h->n_classes ? h->q[c].n : h->runs[c].n;
     o->live[c] = h->mallocs[c] - h->frees[c];
     o->seg_chunks += h->segs[c].n;
     o->spare_chunks += h->spare[c].n;
@@ -401,9 +462,9 @@ void orc_get_stats(const orc_heap *h, orc_stats *o) {
 }
 
 uint64_t orc_queue_items(const orc_heap *h, int c, uint64_t *out, uint64_t max) {
-  uint64_t n = h->q[c].n;
-  for (uint64_t i = 0; i < n && i < max; i++) out[i] = fifo_at(&h->q[c], i);
-  return n;
+  const fifo *f = c < h->n_classes ? &h->q[c] : &h->runs[c];   /* runs: free run starts */
+  for (uint64_t i = 0; i < f->n && i < max; i++) out[i] = fifo_at(f, i);
+  return f->n;
 }
 uint64_t orc_pool_items(const orc_heap *h, uint64_t *out, uint64_t max) {
   for (uint64_t i = 0; i < h->pool.n && i < max; i++) out[i] = fifo_at(&h->pool, i);

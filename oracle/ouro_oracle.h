@@ -58,9 +58,10 @@ typedef struct {
   uint64_t carved_now[ORC_MAX_CLASSES];/* chunks currently owned by the class */
   uint64_t queued[ORC_MAX_CLASSES];    /* entries in the class queue */
   uint64_t live[ORC_MAX_CLASSES];      /* mallocs - frees */
-  uint64_t zero_reqs, too_large;       /* size 0 / size > chunk_bytes requests */
+  uint64_t zero_reqs, too_large;       /* size 0 / size > 1 MiB requests */
   uint64_t bump, pool_size, seg_chunks, spare_chunks;
-  uint32_t error_bits, n_classes;
+  uint32_t error_bits, n_classes;      /* n_classes: classes that fit in one chunk */
+  uint32_t n_large, pad;               /* classes above one chunk (runs of chunks) */
 } orc_stats;
 
 /* chunk_bytes: power of two in [256, 1 MiB]; bytes: multiple of chunk_bytes.
@@ -70,8 +71,9 @@ orc_heap *orc_create(uint64_t bytes, uint64_t chunk_bytes, int variant, uint64_t
 void      orc_destroy(orc_heap *h);
 void      orc_reset(orc_heap *h);
 
-int       orc_num_classes(uint64_t chunk_bytes);
-int       orc_size_class(uint64_t chunk_bytes, uint64_t n);   /* -1 for 0 or > chunk_bytes */
+int       orc_num_classes(uint64_t chunk_bytes);                /* classes within one chunk */
+int       orc_num_large(uint64_t chunk_bytes);                  /* classes above one chunk */
+int       orc_size_class(uint64_t chunk_bytes, uint64_t n);   /* -1 for 0 or > 1 MiB */
 uint64_t  orc_page_bytes(int cls);
 
 /* Returns the byte offset of the block inside the heap, or -1 (null). */
@@ -79,8 +81,9 @@ int64_t   orc_malloc(orc_heap *h, uint64_t n);
 /* Returns 0, or the error bits raised by this call (never aborts). */
 uint32_t  orc_free(orc_heap *h, int64_t off);
 /* Quiescent reclaim: every chunk whose pages are all free leaves its queue
- * and returns to the pool; the pool is sorted and the bump pointer lowered
- * over pooled chunks at its top; virtualized queues are re-laid from position 0. */
+ * and returns to the pool, and so does every chunk of a free run; the pool
+ * is sorted and the bump pointer lowered over pooled chunks at its top;
+ * virtualized queues are re-laid from position 0. */
 void      orc_trim(orc_heap *h);
 
 void      orc_get_stats(const orc_heap *h, orc_stats *out);

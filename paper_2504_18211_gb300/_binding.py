@@ -56,7 +56,7 @@ class Stats(C.Structure):
                [("zero_reqs", C.c_uint64), ("too_large", C.c_uint64), ("bump", C.c_uint64),
                 ("pool_size", C.c_uint64), ("seg_chunks", C.c_uint64), ("spare_chunks", C.c_uint64),
                 ("error_bits", C.c_uint32), ("n_classes", C.c_uint32),
-                ("error_site", C.c_uint32), ("reserved", C.c_uint32)]
+                ("error_site", C.c_uint32), ("n_large", C.c_uint32)]
 
 
 class Snapshot(C.Structure):
@@ -171,11 +171,13 @@ def ouro_heap_device(h: int) -> HeapDev:
 
 
 def _stats_dict(s: Stats) -> dict:
-    nc = s.n_classes
+    """Per-class lists cover every class: those within one chunk (n_classes),
+    then the runs above one chunk (n_large)."""
+    nc = s.n_classes + s.n_large
     out = {k: [int(x) for x in getattr(s, k)[:nc]] for k in
            ("mallocs", "frees", "failed", "carves", "carved_now", "queued", "live", "repushes", "dead")}
     for k in ("zero_reqs", "too_large", "bump", "pool_size", "seg_chunks", "spare_chunks",
-              "error_bits", "n_classes", "error_site"):
+              "error_bits", "n_classes", "n_large", "error_site"):
         out[k] = int(getattr(s, k))
     return out
 
@@ -191,13 +193,7 @@ def ouro_heap_stats_static(h: int, stream=None) -> dict:
 def ouro_heap_stats(h: int, stream=None) -> dict:
     s = Stats()
     load().ouro_heap_stats(C.c_void_p(h), C.byref(s), _stream(stream))
-    nc = s.n_classes
-    out = {k: [int(x) for x in getattr(s, k)[:nc]] for k in
-           ("mallocs", "frees", "failed", "carves", "carved_now", "queued", "live", "repushes", "dead")}
-    for k in ("zero_reqs", "too_large", "bump", "pool_size", "seg_chunks", "spare_chunks",
-              "error_bits", "n_classes", "error_site"):
-        out[k] = int(getattr(s, k))
-    return out
+    return _stats_dict(s)
 
 
 def ouro_heap_snapshot(h: int, stream=None) -> dict:
@@ -213,7 +209,7 @@ def ouro_heap_snapshot(h: int, stream=None) -> dict:
                "chunk_free": (np.ctypeslib.as_array(sn.chunk_free, (nch,)).copy()
                               if sn.chunk_free else None),
                "queues": [np.ctypeslib.as_array(sn.queue[c], (max(sn.queue_n[c], 1),))[:sn.queue_n[c]].copy()
-                          for c in range(nc)]}
+                          for c in range(MAX_CLASSES)]}
     finally:
         lib.ouro_snapshot_free(C.byref(sn))
     return out

@@ -103,16 +103,17 @@ def autotune(Heap, run: BatchRun, heap_bytes: int, chunks=(4096, 8192, 16384, 65
              warps_per_sm=(8, 16, 32, 48, 64), reps: int = 2, max_size: int = 8192):
     """Time the persistent form over chunk size x queue variant x warps per SM.
 
-    A chunk smaller than the largest request cannot serve it (requests above
-    one chunk get null), so such chunk sizes are marked infeasible; a
-    warps-per-SM value above what the kernel's registers allow is marked
-    infeasible too.  Returns (best, table)."""
+    A chunk smaller than the largest request serves those requests as runs
+    of chunks (row "runs": true); requests above 1 MiB cannot be served at
+    all, so max_size above it marks every row infeasible.  A warps-per-SM
+    value above what the kernel's registers allow is marked infeasible too.
+    Returns (best, table)."""
     torch = run.torch
     table = []
     best = None
     for chunk, variant in itertools.product(chunks, variants):
-        if chunk < max_size:
-            table.append({"chunk": chunk, "variant": variant, "status": "infeasible: requests above one chunk"})
+        if max_size > (1 << 20):
+            table.append({"chunk": chunk, "variant": variant, "status": "infeasible: requests above 1 MiB"})
             continue
         heap = Heap(heap_bytes, chunk, variant)
         try:
@@ -126,7 +127,8 @@ def autotune(Heap, run: BatchRun, heap_bytes: int, chunks=(4096, 8192, 16384, 65
                 ms = run.time(heap, "persistent", reps, bps)
                 ok = all(c["mismatches"] == 0 for c in run.checks()) and heap.stats()["error_bits"] == 0
                 row = {"chunk": chunk, "variant": variant, "warps_per_sm": wps, "ms": round(ms, 3),
-                       "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1), "verified": ok}
+                       "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1), "verified": ok,
+                       "runs": max_size > chunk}
                 table.append(row)
                 if ok and (best is None or ms < best["ms"]):
                     best = row

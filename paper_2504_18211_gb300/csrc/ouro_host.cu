@@ -197,7 +197,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   size_t off = 0;
   H->off_qhdr = off;  off = align256(off + sizeof(ouro_qhdr) * d.n_classes);
   H->off_glob = off;  off = align256(off + sizeof(ouro_glob));
-  H->stats_words = (size_t)(d.n_classes + 1) * OURO_NSTAT * OURO_SHARDS;
+  H->stats_words = (size_t)(OURO_MAX_CLASSES + 1) * OURO_NSTAT * OURO_SHARDS;   /* + row OURO_ROW_NONE */
   H->off_stats = off; off = align256(off + H->stats_words * 8);
   H->off_cls = off;   off = align256(off + d.n_chunks);
   H->off_pool = off;  off = align256(off + d.n_chunks * 4);
@@ -308,8 +308,12 @@ __global__ void k_chunk_hist(ouro_heap_dev h, unsigned long long *out) {
   for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < h.n_chunks;
        x += (unsigned long long)gridDim.x * blockDim.x) {
     unsigned c = h.chunk_cls[x];
-    if (c < h.n_classes) atomicAdd(&sh[c], 1ull);
-    else if (c == OURO_CLS_SEG) atomicAdd(&sh[OURO_MAX_CLASSES], 1ull);
+    if (c == OURO_CLS_SEG) {
+      atomicAdd(&sh[OURO_MAX_CLASSES], 1ull);
+      continue;
+    }
+    if (c != OURO_CLS_NONE && (c & 0xC0u) != 0xC0u) c &= 0x3Fu;   /* runs: start (live or free) and body */
+    if (c < OURO_MAX_CLASSES) atomicAdd(&sh[c], 1ull);
   }
   __syncthreads();
   for (unsigned i = threadIdx.x; i <= OURO_MAX_CLASSES; i += blockDim.x)
@@ -328,6 +332,31 @@ __global__ void k_count_spares(ouro_heap_dev h, unsigned long long *out) {
     }
     out[c] = n;
   }
+}
+
+/* free runs on the stack of class c (quiescent); with out_ids, their first
+ * chunks in stack order (at most cap) */
+__device__ unsigned long long walk_runs(const ouro_heap_dev &h, unsigned c, unsigned *out_ids,
+                                        unsigned long long cap) {
+  unsigned x1 = lo32(gl(h)->run_top[c].v);
+  unsigned long long n = 0;
+  while (x1 && n < h.n_chunks) {
+    if (out_ids && n < cap) out_ids[n] = x1 - 1;
+    n++;
+    x1 = *reinterpret_cast<const unsigned *>(h.base + ((size_t)(x1 - 1) << h.log2_chunk));
+  }
+  return n;
+}
+
+/* free runs per class above one chunk, into out[c] (quiescent) */
+__global__ void k_count_runs(ouro_heap_dev h, unsigned long long *out) {
+  for (unsigned c = h.n_classes + threadIdx.x; c < OURO_MAX_CLASSES; c += blockDim.x)
+    out[c] = walk_runs(h, c, nullptr, 0);
+}
+
+__global__ void k_collect_runs(ouro_heap_dev h, int c, unsigned *out, unsigned long long cap,
+                               unsigned long long *n_out) {
+  if (threadIdx.x == 0) *n_out = walk_runs(h, (unsigned)c, out, cap);
 }
 
 struct scratch_buf {
@@ -359,6 +388,8 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
     k_count_spares<<<1, 32, 0, s>>>(d, ds);
     OURO_LAUNCHED();
   }
+  k_count_runs<<<1, 32, 0, s>>>(d, dq);   /* rows n_classes.. of the queued counts */
+  OURO_LAUNCHED();
   std::vector<unsigned long long> hq(nt);
   OURO_CUDA(cudaMemcpyAsync(hq.data(), tmp.p, nt * 8, cudaMemcpyDeviceToHost, s));
   OURO_CUDA(cudaMemcpyAsync(st.data(), d.stats, H->stats_words * 8, cudaMemcpyDeviceToHost, s));
@@ -369,7 +400,8 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
     for (unsigned i = 0; i < OURO_SHARDS; ++i) a += st[((size_t)row * OURO_NSTAT + kind) * OURO_SHARDS + i];
     return a;
   };
-  for (unsigned c = 0; c < d.n_classes; ++c) {
+  out->n_large = OURO_MAX_CLASSES - d.n_classes;
+  for (unsigned c = 0; c < OURO_MAX_CLASSES; ++c) {
     out->mallocs[c] = sum(c, OURO_ST_MALLOC);
     out->frees[c] = sum(c, OURO_ST_FREE);
     out->failed[c] = sum(c, OURO_ST_FAILED);
@@ -379,12 +411,12 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
     out->live[c] = out->mallocs[c] - out->frees[c];
     out->queued[c] = hq[c];
     out->carved_now[c] = hq[(OURO_MAX_CLASSES + 1) + c];
-    out->spare_chunks += hq[2 * (OURO_MAX_CLASSES + 1) + c];
+    if (c < d.n_classes) out->spare_chunks += hq[2 * (OURO_MAX_CLASSES + 1) + c];
   }
   out->seg_chunks = hq[(OURO_MAX_CLASSES + 1) + OURO_MAX_CLASSES];
   if (out->seg_chunks >= out->spare_chunks) out->seg_chunks -= out->spare_chunks;
-  out->zero_reqs = sum(d.n_classes, OURO_ST_ZERO);
-  out->too_large = sum(d.n_classes, OURO_ST_TOO_LARGE);
+  out->zero_reqs = sum(OURO_ROW_NONE, OURO_ST_ZERO);
+  out->too_large = sum(OURO_ROW_NONE, OURO_ST_TOO_LARGE);
   out->bump = g.bump.v < d.n_chunks ? g.bump.v : d.n_chunks;
   out->pool_size = g.pool_taken.v < g.pool_size ? g.pool_size - g.pool_taken.v : 0;
   out->error_bits = g.error_bits;
@@ -432,6 +464,23 @@ extern "C" ouro_status ouro_heap_snapshot(ouro_heap *H, ouro_snapshot *out, void
     OURO_CUDA(cudaMemcpyAsync(&n, cnt.p, 8, cudaMemcpyDeviceToHost, s));
     OURO_CUDA(cudaStreamSynchronize(s));
     if (n > span) n = span;
+    out->queue_n[c] = n;
+    out->queue[c] = (uint32_t *)malloc((n ? n : 1) * 4);
+    if (!out->queue[c]) return OURO_ENOMEM;
+    if (n) OURO_CUDA(cudaMemcpyAsync(out->queue[c], items.p, n * 4, cudaMemcpyDeviceToHost, s));
+    OURO_CUDA(cudaStreamSynchronize(s));
+  }
+  /* classes above one chunk: their free runs (first chunks), stack order */
+  for (unsigned c = d.n_classes; c < OURO_MAX_CLASSES; ++c) {
+    const unsigned long long cap = d.n_chunks;
+    scratch_buf items;
+    OURO_CUDA(cudaMalloc(&items.p, cap * 4));
+    k_collect_runs<<<1, 32, 0, s>>>(d, (int)c, (unsigned *)items.p, cap, (unsigned long long *)cnt.p);
+    OURO_LAUNCHED();
+    unsigned long long n = 0;
+    OURO_CUDA(cudaMemcpyAsync(&n, cnt.p, 8, cudaMemcpyDeviceToHost, s));
+    OURO_CUDA(cudaStreamSynchronize(s));
+    if (n > cap) n = cap;
     out->queue_n[c] = n;
     out->queue[c] = (uint32_t *)malloc((n ? n : 1) * 4);
     if (!out->queue[c]) return OURO_ENOMEM;
@@ -499,6 +548,27 @@ __global__ void k_trim_old_pool(ouro_heap_dev h, unsigned char *in_pool) {
   for (unsigned long long i = pt + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < ps;
        i += (unsigned long long)gridDim.x * blockDim.x)
     in_pool[h.pool[i]] = 1;
+}
+
+/* free runs: every chunk of every run on a class stack joins the pool; the
+ * stacks empty (one thread per class above one chunk) */
+__global__ void k_trim_runs(ouro_heap_dev h, unsigned char *in_pool) {
+  for (unsigned c = h.n_classes + threadIdx.x; c < OURO_MAX_CLASSES; c += blockDim.x) {
+    const unsigned long long k = 1ull << (c - h.n_classes + 1);
+    unsigned long long *top = &gl(h)->run_top[c].v;
+    unsigned x1 = lo32(*top);
+    unsigned long long n = 0;
+    while (x1 && n < h.n_chunks) {
+      const unsigned x = x1 - 1;
+      x1 = *reinterpret_cast<const unsigned *>(h.base + ((size_t)x << h.log2_chunk));
+      for (unsigned long long i = 0; i < k; ++i) {
+        h.chunk_cls[x + i] = OURO_CLS_NONE;
+        in_pool[x + i] = 1;
+      }
+      n++;
+    }
+    *top = pack(hi32(*top) + 1, 0u);
+  }
 }
 
 /* 3. surviving queue items of class c, in queue order, into tmp (one block) */
@@ -695,6 +765,8 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   OURO_LAUNCHED();
   k_trim_old_pool<<<grid, 256, 0, s>>>(d, (unsigned char *)in_pool.p);
   OURO_LAUNCHED();
+  k_trim_runs<<<1, 32, 0, s>>>(d, (unsigned char *)in_pool.p);
+  OURO_LAUNCHED();
   for (unsigned c = 0; c < d.n_classes; ++c) {
     k_trim_compact<<<1, 1024, 0, s>>>(d, (int)c, (const unsigned char *)in_pool.p,
                                       (unsigned *)tmp.p + (size_t)c * span_max, ncount + c);
@@ -770,7 +842,7 @@ static __device__ __align__(256) unsigned long long g_stats_scratch[OURO_STATIC_
 
 /* sum the per-SM shards of every counter row into out[row * OURO_NSTAT + kind] */
 __global__ void k_sum_shards(ouro_heap_dev h, unsigned long long *out) {
-  const unsigned rows = (h.n_classes + 1) * OURO_NSTAT;
+  const unsigned rows = (OURO_MAX_CLASSES + 1) * OURO_NSTAT;   /* every class row + OURO_ROW_NONE */
   for (unsigned i = threadIdx.x; i < rows; i += blockDim.x) {
     unsigned long long a = 0;
     for (unsigned s = 0; s < OURO_SHARDS; ++s) a += h.stats[(size_t)i * OURO_SHARDS + s];
@@ -812,6 +884,8 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
     k_count_spares<<<1, 32, 0, s>>>(d, ds);
     OURO_LAUNCHED();
   }
+  k_count_runs<<<1, 32, 0, s>>>(d, dq);
+  OURO_LAUNCHED();
   unsigned long long hv[OURO_STATIC_SCRATCH_WORDS];
   ouro_glob g;
   OURO_CUDA(cudaMemcpyAsync(hv, scratch, sizeof(hv), cudaMemcpyDeviceToHost, s));
@@ -820,7 +894,8 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
   const unsigned long long *hs = hv, *hq = hv + R * OURO_NSTAT, *hh = hq + R, *hsp = hh + R;
   memset(out, 0, sizeof(*out));
   out->n_classes = d.n_classes;
-  for (unsigned c = 0; c < d.n_classes; ++c) {
+  out->n_large = OURO_MAX_CLASSES - d.n_classes;
+  for (unsigned c = 0; c < OURO_MAX_CLASSES; ++c) {
     const unsigned long long *row = hs + (size_t)c * OURO_NSTAT;
     out->mallocs[c] = row[OURO_ST_MALLOC];
     out->frees[c] = row[OURO_ST_FREE];
@@ -831,12 +906,12 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
     out->live[c] = out->mallocs[c] - out->frees[c];
     out->queued[c] = hq[c];
     out->carved_now[c] = hh[c];
-    out->spare_chunks += hsp[c];
+    if (c < d.n_classes) out->spare_chunks += hsp[c];
   }
   out->seg_chunks = hh[OURO_MAX_CLASSES];
   if (out->seg_chunks >= out->spare_chunks) out->seg_chunks -= out->spare_chunks;
-  out->zero_reqs = hs[(size_t)d.n_classes * OURO_NSTAT + OURO_ST_ZERO];
-  out->too_large = hs[(size_t)d.n_classes * OURO_NSTAT + OURO_ST_TOO_LARGE];
+  out->zero_reqs = hs[(size_t)OURO_ROW_NONE * OURO_NSTAT + OURO_ST_ZERO];
+  out->too_large = hs[(size_t)OURO_ROW_NONE * OURO_NSTAT + OURO_ST_TOO_LARGE];
   out->bump = g.bump.v < d.n_chunks ? g.bump.v : d.n_chunks;
   out->pool_size = g.pool_taken.v < g.pool_size ? g.pool_size - g.pool_taken.v : 0;
   out->error_bits = g.error_bits;

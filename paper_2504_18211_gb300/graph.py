@@ -82,4 +82,6 @@ def expected_class_counts(deg: np.ndarray, chunk_bytes: int, n_classes: int) -> 
         cap[grow] *= 2
     over = np.maximum(deg.astype(np.int64) - max_plain, 0)
     mallocs[n_classes - 1] += int(((over + seg_cap - 1) // seg_cap).sum())
-    return mallocs, frees, cap
+    # the heap reports every class up to 1 MiB (runs of chunks above n_classes): none used here
+    pad = np.zeros(max(0, 17 - n_classes), np.int64)
+    return np.concatenate([mallocs, pad]), np.concatenate([frees, pad]), cap

@@ -17,14 +17,17 @@ def to_dev(a: np.ndarray):
     return torch.from_numpy(a.astype(np.int32, copy=False).view(np.int32)).cuda()
 
 
+ALL_CLASSES = 17            # 16 B .. 1 MiB: classes within a chunk, then runs of chunks
+
+
 def class_of(sizes: np.ndarray, chunk: int) -> np.ndarray:
     """Closed-form class per request (-1: no class); independent of both implementations."""
     s = sizes.astype(np.int64)
     c = np.where(s <= 16, 0, np.ceil(np.log2(np.maximum(s, 1))).astype(np.int64) - 4)
-    return np.where((s == 0) | (s > chunk), -1, c)
+    return np.where((s == 0) | (s > (1 << 20)), -1, c)
 
 
-def per_class_counts(sizes: np.ndarray, chunk: int, n_classes: int) -> list:
+def per_class_counts(sizes: np.ndarray, chunk: int, n_classes: int = ALL_CLASSES) -> list:
     c = class_of(sizes, chunk)
     return [int((c == k).sum()) for k in range(n_classes)]
 
@@ -39,7 +42,9 @@ def assert_no_overlap(ptrs: np.ndarray, sizes: np.ndarray, base: int, heap_bytes
     page = (np.uint64(16) << cls[live].astype(np.uint64)).astype(np.uint64)
     off = p[live] - np.uint64(base)
     assert np.all(off < np.uint64(heap_bytes)), "block outside the heap"
-    assert np.all(off % page == 0), "block not aligned to its class"
+    align = np.minimum(page, np.uint64(chunk))           # runs of chunks start on a chunk
+    assert np.all(off % align == 0), "block not aligned to its class"
+    assert np.all(off + page <= np.uint64(heap_bytes)), "block runs past the heap"
     order = np.argsort(off, kind="stable")
     o, pg = off[order], page[order]
     if o.size > 1:

@@ -4,11 +4,13 @@ Each pin takes the path of an oracle build so that the mutation test can run
 the same pins against deliberately broken builds (tests/test_oracle_mutants.py).
 
 What pins what:
-  class map          closed form ceil(log2 n) - 4 over every n in [0, chunk+1]
+  class map          closed form ceil(log2 n) - 4 over every n in [0, chunk+1] and
+                     past it up to 1 MiB (runs of chunks), null above
   layout / address   a single-class fill of a tiny heap returns exactly the
                      multiples of the page size in [0, bytes)
   capacity           closed form n_chunks * chunk / page; page-array limit
-                     floor(min(bytes/page, cap) / ppc) * ppc
+                     floor(min(bytes/page, cap) / ppc) * ppc; runs: floor(n_chunks / k)
+                     and freed runs reused before the bump pointer moves
   queue semantics    brute force against a set allocator (tests/setmodel.py)
   small workload     closed form of the 10,240 x 16 B run (tests/golden/c0_small.json)
   restore            free everything, trim: the state equals the post-create state
@@ -43,11 +45,12 @@ def pin_class_map(lib_path):
     lib = oracle.load(lib_path)
     for chunk in (256, 1024, 8192, 65536, 1 << 20):
         assert lib.orc_num_classes(chunk) == ceil_log2(chunk) - 3
-        ns = range(0, chunk + 2) if chunk <= 65536 else \
-            list(range(0, 4097)) + [chunk - 1, chunk, chunk + 1] + [2 ** k + d for k in range(5, 20) for d in (-1, 0, 1)]
+        assert lib.orc_num_large(chunk) == 17 - (ceil_log2(chunk) - 3)
+        ns = list(range(0, chunk + 2)) if chunk <= 65536 else list(range(0, 4097))
+        ns += [chunk - 1, chunk, chunk + 1] + [2 ** k + d for k in range(5, 21) for d in (-1, 0, 1)]
         for n in ns:
             c = lib.orc_size_class(chunk, n)
-            if n == 0 or n > chunk:
+            if n == 0 or n > (1 << 20):
                 assert c == -1, (chunk, n, c)
             else:
                 assert c == max(0, ceil_log2(n) - 4), (chunk, n, c)
@@ -97,6 +100,21 @@ def pin_capacity(lib_path):
         got = sum(1 for _ in range(5000) if h.malloc(16) >= 0)
         qc = min(64 * 1024 // 16, cap)
         assert got == (qc // 64) * 64, (cap, got)
+    # runs above one chunk: 3000 B on 1 KiB chunks is a 4 KiB run of 4 chunks
+    # (class 8); 64 chunks hold floor(64 / 4) = 16 runs, each at the next bump
+    # position; freed runs are reused (last freed first) without moving the bump
+    for variant in ALL_VARIANTS:
+        h = heap(lib_path, 64 * 1024, 1024, variant)
+        offs = [h.malloc(3000) for _ in range(20)]
+        assert offs[:16] == [4096 * i for i in range(16)] and offs[16:] == [-1] * 4, (variant, offs)
+        st = h.stats()
+        assert st["mallocs"][8] == 16 and st["failed"][8] == 4 and st["carved_now"][8] == 64, (variant, st)
+        for o in offs[:16]:
+            assert h.free(o) == 0
+        assert h.free(offs[3]) == oracle.ERR_DOUBLE_FREE and h.free(offs[3] + 1024) == oracle.ERR_BAD_FREE
+        again = [h.malloc(2049) for _ in range(16)]         # 2049 B: the same class
+        assert again == offs[15::-1], (variant, again)
+        assert h.stats()["bump"] == 64 and h.malloc(16) == -1
 
 
 def _run_sequence(lib_path, variant, bytes_, chunk, ops, model_nulls=True):
@@ -104,7 +122,7 @@ def _run_sequence(lib_path, variant, bytes_, chunk, ops, model_nulls=True):
     model_nulls=False (virtualized queues, whose segments hold chunks of the
     same heap): blocks and counts are checked, null answers only counted."""
     h = heap(lib_path, bytes_, chunk, variant)
-    m = SetModel(bytes_, chunk)
+    m = SetModel(bytes_, chunk, strict_frontier=model_nulls)
     order = []   # live offsets in allocation order
     freed = []   # offsets freed at least once
     for op, arg in ops:
@@ -168,7 +186,7 @@ def pin_brute_force(lib_path, max_len=4, random_runs=60, random_len=250):
             for _ in range(random_len):
                 r = rng.random()
                 if r < 0.55:
-                    ops.append(("m", int(rng.choice([1, 16, 20, 32, 50, 64, 120, 128, 200, 256]))))
+                    ops.append(("m", int(rng.choice([1, 16, 20, 32, 50, 64, 120, 128, 200, 256, 300, 700, 1100]))))
                 elif r < 0.90:
                     ops.append(("f", int(rng.integers(0, 1000))))
                 elif r < 0.93:
@@ -215,7 +233,8 @@ def pin_restore(lib_path):
         live = []
         for _ in range(3000):
             if rng.random() < 0.6 or not live:
-                o = h.malloc(int(rng.integers(1, chunk + 1)))
+                n = int(rng.integers(1, chunk + 1)) if rng.random() < 0.9 else int(rng.integers(chunk + 1, 4 * chunk))
+                o = h.malloc(n)
                 assert o >= 0
                 if o >= 0:
                     live.append(o)

@@ -5,7 +5,13 @@ the size class the chunk was given.  A request of class c can be served iff
 some chunk of class c still has a page that is not live, or a chunk that no
 class owns is left (and, for page-array queues, the class still has room
 under its queue capacity).  The allocator must take a new chunk only when the
-first condition fails.  Nothing here is shared with the oracle.
+first condition fails.
+
+Classes above one chunk are runs of 2^(c - C + 1) contiguous chunks (C =
+classes within a chunk): a run that is owned but not live must be reused
+before a new one is cut, and a new run starts at the frontier -- one past the
+highest owned chunk -- where contiguous free chunks are certain.  Nothing here
+is shared with the oracle.
 """
 from __future__ import annotations
 
@@ -14,22 +20,69 @@ def ceil_log2(n: int) -> int:
     return (n - 1).bit_length()
 
 
+MAX_REQUEST = 1 << 20
+ALL_CLASSES = 17
+
+
 class SetModel:
-    def __init__(self, bytes_: int, chunk_bytes: int, page_array_cap: int | None = None):
+    def __init__(self, bytes_: int, chunk_bytes: int, page_array_cap: int | None = None,
+                 strict_frontier: bool = True):
         self.bytes, self.chunk = bytes_, chunk_bytes
         self.n_chunks = bytes_ // chunk_bytes
         self.owner = [-1] * self.n_chunks
         self.live: dict[int, int] = {}
+        self.run_start: dict[int, int] = {}      # first chunk of each owned run -> class
         self.page_array_cap = page_array_cap
-        nc = ceil_log2(chunk_bytes) - 4 + 1
-        self.mallocs = [0] * nc
-        self.frees = [0] * nc
-        self.failed = [0] * nc
+        # strict_frontier=False: the allocator may own chunks this model does
+        # not see (queue segments), so a new run may start above the frontier
+        self.strict_frontier = strict_frontier
+        self.C = ceil_log2(chunk_bytes) - 4 + 1
+        self.mallocs = [0] * ALL_CLASSES
+        self.frees = [0] * ALL_CLASSES
+        self.failed = [0] * ALL_CLASSES
 
     def cls(self, n: int):
-        if n == 0 or n > self.chunk:
+        if n == 0 or n > MAX_REQUEST:
             return None
         return max(0, ceil_log2(n) - 4)
+
+    def run_chunks(self, c: int) -> int:
+        return self.page(c) // self.chunk
+
+    def frontier(self) -> int:
+        owned = [x for x in range(self.n_chunks) if self.owner[x] >= 0]
+        return max(owned) + 1 if owned else 0
+
+    def free_run_of(self, c: int) -> bool:
+        return any(rc == c and x * self.chunk not in self.live for x, rc in self.run_start.items())
+
+    def check_run_malloc(self, c: int, off: int) -> None:
+        k = self.run_chunks(c)
+        if off == -1:
+            assert not self.free_run_of(c), f"null for class {c} with a free run"
+            if self.strict_frontier:
+                assert self.frontier() + k > self.n_chunks, f"null for class {c} with room at the frontier"
+            self.failed[c] += 1
+            return
+        assert 0 <= off < self.bytes and off % self.chunk == 0, "run not at a chunk start"
+        assert off not in self.live, "run handed out twice"
+        x = off // self.chunk
+        if x in self.run_start:
+            assert self.run_start[x] == c, "run of another class"
+        else:
+            assert not self.free_run_of(c), "new run cut while the class had a free run"
+            if self.strict_frontier:
+                assert x == self.frontier(), "new run not at the frontier"
+            assert x + k <= self.n_chunks, "run past the heap"
+            assert all(self.owner[x + i] == -1 for i in range(k)), "run over owned chunks"
+            for i in range(k):
+                self.owner[x + i] = c
+            self.run_start[x] = c
+        end = off + self.page(c)
+        for o, oc in self.live.items():
+            assert end <= o or o + self.page(oc) <= off, "live blocks overlap"
+        self.live[off] = c
+        self.mallocs[c] += 1
 
     def page(self, c: int) -> int:
         return 16 * 2 ** c
@@ -58,6 +111,9 @@ class SetModel:
         if c is None:
             assert off == -1, f"malloc({n}) must be null"
             return
+        if c >= self.C:
+            self.check_run_malloc(c, off)
+            return
         if off == -1:
             assert not self.class_has_free_page(c), f"null for class {c} with a free page"
             assert not self.can_take_chunk(c), f"null for class {c} with a chunk left"
@@ -83,6 +139,10 @@ class SetModel:
         if off < 0 or off >= self.bytes:
             return 1
         x = off // self.chunk
+        if self.owner[x] >= self.C:
+            if x not in self.run_start or off % self.chunk:
+                return 1
+            return 0 if off in self.live else 2
         if self.owner[x] < 0 or off % self.page(self.owner[x]):
             return 1
         if off not in self.live:
@@ -95,5 +155,10 @@ class SetModel:
 
     def trim(self) -> None:
         for x in range(self.n_chunks):
-            if self.owner[x] >= 0 and not any(o // self.chunk == x for o in self.live):
+            if 0 <= self.owner[x] < self.C and not any(o // self.chunk == x for o in self.live):
                 self.owner[x] = -1
+        for x, c in list(self.run_start.items()):
+            if x * self.chunk not in self.live:
+                for i in range(self.run_chunks(c)):
+                    self.owner[x + i] = -1
+                del self.run_start[x]
