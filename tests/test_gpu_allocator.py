@@ -216,7 +216,7 @@ def test_divergent_and_partial_warps(ouro, variant):
     bytes_, chunk = 16 << 20, 8192
     sizes = W.sweep_sizes(4096, seed=5)
     sizes[1::2] = 0                       # half the lanes ask for nothing
-    sizes[100] = 9000                     # above one chunk
+    sizes[100] = 2 << 20                  # above the largest class (1 MiB)
     with ouro.Heap(bytes_, chunk, variant) as heap:
         ptrs = heap.malloc(to_dev(sizes))
         one = heap.malloc(to_dev(np.array([24], np.uint32)))
