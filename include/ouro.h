@@ -132,7 +132,7 @@ typedef struct {
   uint32_t error_bits, n_classes;         /* n_classes: classes that fit in one chunk */
   uint32_t error_site;                    /* where the first error was recorded (device header's OURO_SITE_*) */
   uint32_t n_large;                       /* classes above one chunk: entries n_classes .. n_classes+n_large-1
-                                             of the per-class arrays; queued = free runs of the class */
+                                             of the per-class arrays; queued = free runs in the class queue */
 } ouro_stats;
 
 /* Host copy of the queue state, for tests (ouro_heap_snapshot).  Arrays are
@@ -154,10 +154,11 @@ typedef struct {
  * i.e. 16 << c bytes (Sec. 4.2: queues of power-of-two sizes).  Classes that
  * fit in one chunk (c < n_classes = log2(chunk_bytes) - 3) are pages of chunks
  * served by the class queues.  Larger classes (the paper is silent on them)
- * are runs of 2^(c - n_classes + 1) contiguous chunks: a freed run waits on
- * its class's stack for reuse; a new run is cut at the bump pointer (pooled
- * chunks are not gathered into runs); ouro_heap_trim returns free runs to the
- * pool.  0 bytes and more than 1 MiB: null, counted. */
+ * are runs of 2^(c - n_classes + 1) contiguous chunks: a freed run waits in
+ * its class queue (same queue form as the other classes) for reuse; a debt
+ * is carved by cutting runs at the bump pointer (pooled chunks are not
+ * gathered into runs); ouro_heap_trim returns free runs to the pool.
+ * 0 bytes and more than 1 MiB: null, counted. */
 
 /* ---- heap life cycle (Sec. 1: the host preallocates the heap) ---------- */
 

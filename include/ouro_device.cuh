@@ -96,8 +96,6 @@ struct ouro_glob {
   unsigned long long pool_size;
   unsigned int error_bits;
   unsigned int error_site;   /* OURO_SITE_* of the first error */
-  ouro_line run_top[OURO_MAX_CLASSES];   /* classes above one chunk: free-run stack,
-                                            (tag << 32) | (first chunk + 1), 0 = empty */
 };
 
 /* header of a virtualized-list segment (first 64 bytes of its chunk) */
@@ -867,6 +865,94 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
   if ((int)lane == owner) unlock(&q->lock.v);
 }
 
+/* ------------------------------------------- run queues: carve batch */
+/* Carve for a class above one chunk; called like page_carve (lane `owner`
+ * holds the carve lock of class c).  The lock holder cuts every run the
+ * class's debt needs -- m runs of k contiguous chunks -- with one
+ * compare-and-swap at the bump pointer (pooled chunks are never gathered
+ * into runs), and the warp writes the runs' first chunks into the debt
+ * slots; the rest of the debt gets null markers once the heap is exhausted. */
+template <int V>
+__device__ __noinline__ void run_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
+  ouro_qhdr *q = qh(h, c);
+  ouro_glob *g = gl(h);
+  const unsigned lane = laneid();
+  const unsigned k_log = (unsigned)c - h.n_classes + 1;
+  unsigned long long m = 0, b = 0, t0 = 0;
+  int exhausted = 0;
+  if ((int)lane == owner) {
+    const unsigned long long t = ld_acq(&q->tail.v), hd = ld_acq(&q->head.v);
+    if (hd > t) {
+      const unsigned long long want = min(hd - t, (unsigned long long)h.max_carve);
+      seg_prepare<QF>(h, c, t, t + want - 1);       /* queue storage first */
+      b = ld_rlx(&g->bump.v);
+      for (unsigned it = 0; it < h.spin_limit; ++it) {
+        const unsigned long long avail = b < h.n_chunks ? (h.n_chunks - b) >> k_log : 0;
+        const unsigned long long mm = min(want, avail);
+        if (!mm) break;
+        const unsigned long long seen = atomicCAS(&g->bump.v, b, b + (mm << k_log));
+        if (seen == b) {
+          m = mm;
+          break;
+        }
+        b = seen;
+      }
+      exhausted = m < want;
+      if (m) {
+        t0 = atomicAdd(&q->tail.v, m);
+        stat_add(h, c, OURO_ST_CARVE, m << k_log);
+      }
+    }
+  }
+  m = __shfl_sync(vmask, m, owner);
+  b = __shfl_sync(vmask, b, owner);
+  t0 = __shfl_sync(vmask, t0, owner);
+  exhausted = __shfl_sync(vmask, exhausted, owner);
+  const unsigned nl = __popc(vmask), rk = __popc(vmask & lanemask_lt());
+  if (m) {
+    const unsigned long long nch = m << k_log;
+    for (unsigned long long i = rk; i < nch; i += nl)
+      h.chunk_cls[b + i] = (unsigned char)((i & ((1ull << k_log) - 1)) ? (OURO_CLS_RUN_BODY | c)
+                                                                        : (OURO_CLS_RUN_FREE | c));
+    __threadfence();
+    __syncwarp(vmask);
+    for (unsigned long long i0 = 0; i0 < m; i0 += nl) {
+      const unsigned long long i = i0 + rk;
+      const bool act = i < m;
+      unsigned long long *cell = act ? slot_at<QF>(h, c, t0 + i, true) : nullptr;
+      int rc = 0;
+      if (cell) rc = put_at(h, cell, t0 + i, (unsigned)(b + (i << k_log)), false, VL);
+      if (VL) seg_event_warp<QF>(h, c, cell, act, vmask);
+      if (cell && rc == 1) push_one<QF>(h, c, (unsigned)(b + (i << k_log)));
+    }
+  }
+  if (exhausted) {
+    unsigned long long dt = 0, dn = 0;
+    if ((int)lane == owner) {
+      for (unsigned it = 0; it < h.spin_limit; ++it) {
+        const unsigned long long t = ld_acq(&q->tail.v), hd = ld_acq(&q->head.v);
+        if (hd <= t) break;
+        seg_prepare<QF>(h, c, t, hd - 1);
+        if (atomicCAS(&q->tail.v, t, hd) == t) { dt = t; dn = hd - t; break; }
+      }
+      stat_add(h, c, OURO_ST_DEAD, dn);
+    }
+    dt = __shfl_sync(vmask, dt, owner);
+    dn = __shfl_sync(vmask, dn, owner);
+    for (unsigned long long i0 = 0; i0 < dn; i0 += nl) {
+      const unsigned long long i = i0 + rk;
+      const bool act = i < dn;
+      unsigned long long *cell = act ? slot_at<QF>(h, c, dt + i, true) : nullptr;
+      if (cell) put_at(h, cell, dt + i, 0, true, VL);
+      if (VL) seg_event_warp<QF>(h, c, cell, act, vmask);
+    }
+  }
+  __syncwarp(vmask);
+  if ((int)lane == owner) unlock(&q->lock.v);
+}
+
 /* --------------------------------------------------------- page queues */
 /* Every lane of vmask calls.  A lane with cls >= 0 asks for a page of that
  * class (any mix of classes); a lane with cls < 0 asks for nothing and only
@@ -920,7 +1006,9 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
         while (lockers) {
           const int j = __ffs(lockers) - 1;
           lockers &= lockers - 1;
-          page_carve<V>(h, __shfl_sync(vmask, cls, j), vmask, j);
+          const int cj = __shfl_sync(vmask, cls, j);
+          if (cj >= (int)h.n_classes) run_carve<V>(h, cj, vmask, j);
+          else page_carve<V>(h, cj, vmask, j);
         }
       }
       const unsigned waiting = __ballot_sync(vmask, st == 0);
@@ -950,14 +1038,19 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
 
   void *res = nullptr;
   if (st == 1) {
-    if (h.checked) {
-      unsigned pg = item & ((1u << (h.log2_chunk - 4 - cls)) - 1);
-      unsigned x = item >> (h.log2_chunk - 4 - cls);
-      unsigned bit = 1u << (pg & 31);
-      unsigned old = atomicAnd(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], ~bit);
-      if (!(old & bit)) set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_CHECKED);
+    if (cls >= (int)h.n_classes) {          /* a run: item is its first chunk, live again */
+      h.chunk_cls[item] = (unsigned char)cls;
+      res = h.base + ((size_t)item << h.log2_chunk);
+    } else {
+      if (h.checked) {
+        unsigned pg = item & ((1u << (h.log2_chunk - 4 - cls)) - 1);
+        unsigned x = item >> (h.log2_chunk - 4 - cls);
+        unsigned bit = 1u << (pg & 31);
+        unsigned old = atomicAnd(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], ~bit);
+        if (!(old & bit)) set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_CHECKED);
+      }
+      res = h.base + ((size_t)item << (4 + cls));
     }
-    res = h.base + ((size_t)item << (4 + cls));
   }
   /* per-class counters, one update per class group of the warp */
   const unsigned g2 = warp_group(h, vmask, cls);
@@ -1022,78 +1115,30 @@ __device__ __forceinline__ int locate(const ouro_heap_dev &h, const void *p, uns
 
 /* ------------------------------------------------ runs above one chunk */
 /* Requests above one chunk (the paper is silent on them): class c >=
- * n_classes is a run of 2^(c - n_classes + 1) contiguous chunks.  Freed runs
- * wait on a per-class stack (tagged; the link lives in the run's first
- * word); a new run is cut at the bump pointer by compare-and-swap, so it is
- * contiguous and never runs past the heap.  One lane per request: large
- * requests are few and each moves many bytes. */
-__device__ inline void *run_malloc(const ouro_heap_dev &h, int c) {
-  ouro_glob *g = gl(h);
-  unsigned long long *top = &g->run_top[c].v;
-  const unsigned long long k = 1ull << (c - (int)h.n_classes + 1);
-  for (unsigned it = 0; it < h.spin_limit; ++it) {
-    const unsigned long long old = ld_acq(top);
-    if (!lo32(old)) break;
-    const unsigned x = lo32(old) - 1;
-    const unsigned nxt = *(volatile unsigned *)(h.base + ((size_t)x << h.log2_chunk));
-    if (cas_ar(top, old, pack(hi32(old) + 1, nxt)) == old) {
-      h.chunk_cls[x] = (unsigned char)c;                 /* live again */
-      __threadfence();
-      stat_add(h, c, OURO_ST_MALLOC, 1);
-      return h.base + ((size_t)x << h.log2_chunk);
-    }
-  }
-  unsigned long long b = ld_rlx(&g->bump.v);
-  for (unsigned it = 0; it < h.spin_limit && b + k <= h.n_chunks; ++it) {
-    const unsigned long long seen = atomicCAS(&g->bump.v, b, b + k);
-    if (seen == b) {
-      for (unsigned long long i = 1; i < k; ++i) h.chunk_cls[b + i] = (unsigned char)(OURO_CLS_RUN_BODY | c);
-      h.chunk_cls[b] = (unsigned char)c;
-      __threadfence();
-      stat_add(h, c, OURO_ST_MALLOC, 1);
-      stat_add(h, c, OURO_ST_CARVE, k);
-      return h.base + ((size_t)b << h.log2_chunk);
-    }
-    b = seen;
-  }
-  stat_add(h, c, OURO_ST_FAILED, 1);
-  return nullptr;
-}
+ * n_classes is a run of 2^(c - n_classes + 1) contiguous chunks.  Its class
+ * queue, in the heap's queue form like every other class, holds the first
+ * chunks of free runs; a debt is carved by cutting runs at the bump pointer
+ * (run_carve).  The class byte of a run's first chunk tells a live run (c)
+ * from a free one (RUN_FREE | c), so that a second free is seen. */
 
-/* Free the run of class c starting at chunk x: its class byte turns from
- * c to RUN_FREE | c in one compare-and-swap of the word holding it (so a
- * second free of the same run is seen), then the run goes on the stack. */
-__device__ inline void run_free(const ouro_heap_dev &h, int c, unsigned x) {
+/* Mark run x of class c free: its class byte turns from c to RUN_FREE | c
+ * in one compare-and-swap of the word holding it.  False (error recorded)
+ * when the run is already free or x is no run start. */
+__device__ inline bool run_mark_free(const ouro_heap_dev &h, int c, unsigned x) {
   unsigned *w = reinterpret_cast<unsigned *>(h.chunk_cls + (x & ~3u));
   const unsigned sh = (x & 3u) * 8u;
-  bool ok = false;
   for (unsigned it = 0; it < h.spin_limit; ++it) {
     const unsigned v = *(volatile unsigned *)w;
     const unsigned byte = (v >> sh) & 0xFFu;
     if (byte != (unsigned)c) {
       set_error(h, byte == (OURO_CLS_RUN_FREE | (unsigned)c) ? OURO_ERR_DOUBLE_FREE : OURO_ERR_BAD_FREE,
                 OURO_SITE_RUN_FREE);
-      return;
+      return false;
     }
-    if (atomicCAS(w, v, (v & ~(0xFFu << sh)) | ((OURO_CLS_RUN_FREE | (unsigned)c) << sh)) == v) {
-      ok = true;
-      break;
-    }
-  }
-  if (!ok) {
-    set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_RUN_FREE);
-    return;
-  }
-  stat_add(h, c, OURO_ST_FREE, 1);
-  unsigned long long *top = &gl(h)->run_top[c].v;
-  volatile unsigned *link = reinterpret_cast<volatile unsigned *>(h.base + ((size_t)x << h.log2_chunk));
-  for (unsigned it = 0; it < h.spin_limit; ++it) {
-    const unsigned long long old = ld_acq(top);
-    *link = lo32(old);
-    __threadfence();
-    if (cas_ar(top, old, pack(hi32(old) + 1, x + 1)) == old) return;
+    if (atomicCAS(w, v, (v & ~(0xFFu << sh)) | ((OURO_CLS_RUN_FREE | (unsigned)c) << sh)) == v) return true;
   }
   set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_RUN_FREE);
+  return false;
 }
 
 /* ------------------------------------------------------- chunk queues */
@@ -1522,6 +1567,26 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
   if (cls >= 0 && lane == (unsigned)(__ffs(sg) - 1)) stat_add(h, cls, OURO_ST_FREE, __popc(sg));
 }
 
+/* Chunk-queue heaps: classes within a chunk go to the chunk queues, runs
+ * above one chunk to their page-style run queues.  Every lane of mask calls. */
+template <int V>
+__device__ void *chunk_or_run_malloc(const ouro_heap_dev &h, int cls, unsigned mask) {
+  const int pc = cls < (int)h.n_classes ? cls : -1;
+  const int rc = cls >= (int)h.n_classes ? cls : -1;
+  void *a = nullptr, *b = nullptr;
+  if (__any_sync(mask, pc >= 0)) a = chunk_malloc<V>(h, pc, mask);
+  if (__any_sync(mask, rc >= 0)) b = page_malloc<V>(h, rc, mask);
+  return rc >= 0 ? b : a;
+}
+
+/* cls: the block's class, its run already marked free (runs), or -1 */
+template <int V>
+__device__ void chunk_or_run_free(const ouro_heap_dev &h, int cls, unsigned item, const void *p, unsigned mask) {
+  chunk_free_impl<V>(h, cls < (int)h.n_classes ? cls : -1, p, mask);
+  const unsigned rm = __ballot_sync(mask, cls >= (int)h.n_classes);
+  if (rm && ((rm >> laneid()) & 1)) page_free<V>(h, cls, item, rm);
+}
+
 }  // namespace detail
 }  // namespace ouro
 
@@ -1551,12 +1616,6 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   int cls = want ? size_class(h, n) : -1;
   if (want && cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
-  void *run = nullptr;
-  const bool is_run = cls >= (int)h.n_classes;
-  if (is_run) {                       /* above one chunk: a run, then help the others */
-    run = run_malloc(h, cls);
-    cls = -1;
-  }
   const unsigned g = __match_any_sync(mask, cls);
   const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
   unsigned have = 0, take = 0;
@@ -1585,7 +1644,7 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
     void *p = page_malloc<V>(h, rest, mask);
     if (rest >= 0) res = p;
   }
-  return is_run ? run : res;
+  return res;
 }
 
 /* staged free for page queues; every lane of the warp's call mask calls */
@@ -1599,8 +1658,7 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (cls >= (int)h.n_classes) {
-      run_free(h, cls, item);
-      cls = -1;
+      if (!run_mark_free(h, cls, item)) cls = -1;
     } else if (h.checked) {
       const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
       const unsigned bit = 1u << (pg & 31);
@@ -1615,7 +1673,7 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
   const unsigned g = __match_any_sync(mask, cls);
   const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
   unsigned have = 0, take = 0;
-  if (cls >= 0 && lane == leader) {
+  if (cls >= 0 && cls < (int)h.n_classes && lane == leader) {   /* runs are not staged */
     have = ctx.cnt[w][cls];
     take = min(OURO_STAGE_CAP - have, k);
     ctx.cnt[w][cls] = (unsigned char)(have + take);
@@ -1672,27 +1730,19 @@ __device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev
 static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t n) {
   using namespace ouro::detail;
   const unsigned mask = __activemask();
-  int cls = size_class(h, n);
+  const int cls = size_class(h, n);
   if (cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
-  void *run = nullptr;
-  const bool is_run = cls >= (int)h.n_classes;
-  if (is_run) {                       /* above one chunk: a run of chunks */
-    run = run_malloc(h, cls);
-    cls = -1;
-  }
-  if (!__any_sync(mask, cls >= 0)) return run;
+  if (!__any_sync(mask, cls >= 0)) return nullptr;
   /* lanes without a class stay in as helpers of the warp's carves */
-  void *r;
   switch (h.variant) {
-    case OURO_PAGE_ARRAY: r = page_malloc<OURO_PAGE_ARRAY>(h, cls, mask); break;
-    case OURO_PAGE_VLIST: r = page_malloc<OURO_PAGE_VLIST>(h, cls, mask); break;
-    case OURO_CHUNK_ARRAY: r = chunk_malloc<OURO_CHUNK_ARRAY>(h, cls, mask); break;
-    case OURO_CHUNK_VLIST: r = chunk_malloc<OURO_CHUNK_VLIST>(h, cls, mask); break;
-    case OURO_PAGE_VARRAY: r = page_malloc<OURO_PAGE_VARRAY>(h, cls, mask); break;
-    case OURO_CHUNK_VARRAY: r = chunk_malloc<OURO_CHUNK_VARRAY>(h, cls, mask); break;
-    default: r = nullptr;
+    case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, mask);
+    case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, mask);
+    case OURO_PAGE_VARRAY: return page_malloc<OURO_PAGE_VARRAY>(h, cls, mask);
+    case OURO_CHUNK_ARRAY: return chunk_or_run_malloc<OURO_CHUNK_ARRAY>(h, cls, mask);
+    case OURO_CHUNK_VLIST: return chunk_or_run_malloc<OURO_CHUNK_VLIST>(h, cls, mask);
+    case OURO_CHUNK_VARRAY: return chunk_or_run_malloc<OURO_CHUNK_VARRAY>(h, cls, mask);
+    default: return nullptr;
   }
-  return is_run ? run : r;
 }
 
 /* Return a block to the heap; null is ignored; a pointer that is not a live
@@ -1706,8 +1756,7 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (cls >= (int)h.n_classes) {   /* a run */
-      run_free(h, cls, item);
-      cls = -1;
+      if (!run_mark_free(h, cls, item)) cls = -1;
     } else if (h.checked && ouro_page_queues((int)h.variant)) {
       unsigned ppcm = (1u << (h.log2_chunk - 4 - cls)) - 1;
       unsigned pg = item & ppcm, x = item >> (h.log2_chunk - 4 - cls);
@@ -1717,9 +1766,9 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
       if (old & bit) { set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_DOUBLE); cls = -1; }
     }
   }
-  if (h.variant == OURO_CHUNK_ARRAY) { chunk_free_impl<OURO_CHUNK_ARRAY>(h, cls, p, mask); return; }
-  if (h.variant == OURO_CHUNK_VLIST) { chunk_free_impl<OURO_CHUNK_VLIST>(h, cls, p, mask); return; }
-  if (h.variant == OURO_CHUNK_VARRAY) { chunk_free_impl<OURO_CHUNK_VARRAY>(h, cls, p, mask); return; }
+  if (h.variant == OURO_CHUNK_ARRAY) { chunk_or_run_free<OURO_CHUNK_ARRAY>(h, cls, item, p, mask); return; }
+  if (h.variant == OURO_CHUNK_VLIST) { chunk_or_run_free<OURO_CHUNK_VLIST>(h, cls, item, p, mask); return; }
+  if (h.variant == OURO_CHUNK_VARRAY) { chunk_or_run_free<OURO_CHUNK_VARRAY>(h, cls, item, p, mask); return; }
   const unsigned vmask = __ballot_sync(mask, cls >= 0);
   if (cls < 0) return;
   switch (h.variant) {

@@ -13,7 +13,7 @@
 
 #define CLS_NONE (-1)   /* chunk never carved, or back in the pool */
 #define CLS_SEG  (-2)   /* chunk holds a segment of a virtualized queue */
-#define CLS_RUN_FREE 64   /* + class: first chunk of a free run (on its class stack) */
+#define CLS_RUN_FREE 64   /* + class: first chunk of a free run (in its class queue) */
 #define CLS_RUN_BODY 128  /* + class: second or later chunk of a run */
 #define MAX_REQUEST (16ull << (ORC_MAX_CLASSES - 1))   /* 1 MiB */
 
@@ -62,7 +62,6 @@ struct orc_heap {
   fifo segs[ORC_MAX_CLASSES];
   uint64_t seg_first[ORC_MAX_CLASSES];
   fifo spare[ORC_MAX_CLASSES];
-  fifo runs[ORC_MAX_CLASSES];   /* classes above one chunk: free runs, used as a stack */
   uint64_t carved_now[ORC_MAX_CLASSES];
   uint64_t mallocs[ORC_MAX_CLASSES], frees[ORC_MAX_CLASSES], failed[ORC_MAX_CLASSES],
            carves[ORC_MAX_CLASSES];
@@ -152,7 +151,7 @@ orc_heap *orc_create(uint64_t bytes, uint64_t chunk_bytes, int variant, uint64_t
 void orc_destroy(orc_heap *h) {
   if (!h) return;
   for (int c = 0; c < ORC_MAX_CLASSES; c++) {
-    fifo_free(&h->q[c]); fifo_free(&h->segs[c]); fifo_free(&h->spare[c]); fifo_free(&h->runs[c]);
+    fifo_free(&h->q[c]); fifo_free(&h->segs[c]); fifo_free(&h->spare[c]);
   }
   fifo_free(&h->pool);
   free(h->chunk_cls); free(h->live); free(h->free_pages); free(h->bits);
@@ -166,7 +165,7 @@ void orc_reset(orc_heap *h) {
   if (h->free_pages) memset(h->free_pages, 0, h->n_chunks * sizeof(uint32_t));
   if (h->bits) memset(h->bits, 0, h->n_chunks * h->words_per_chunk * sizeof(uint64_t));
   for (int c = 0; c < ORC_MAX_CLASSES; c++) {
-    fifo_clear(&h->q[c]); fifo_clear(&h->segs[c]); fifo_clear(&h->spare[c]); fifo_clear(&h->runs[c]);
+    fifo_clear(&h->q[c]); fifo_clear(&h->segs[c]); fifo_clear(&h->spare[c]);
     h->qhead[c] = h->qtail[c] = h->seg_first[c] = 0;
     h->carved_now[c] = h->mallocs[c] = h->frees[c] = h->failed[c] = h->carves[c] = 0;
   }
@@ -263,23 +262,29 @@ static int carve(orc_heap *h, int c) {
 }
 
 /* ---------------------------------------------- runs above one chunk */
-/* A request above one chunk takes a run of run_chunks(c) contiguous chunks:
- * the last freed run of its class first; else a run cut at the bump
- * pointer, the only place where contiguous chunks are sure to be free
- * (pooled chunks are not reused for runs).  Reading: the paper is silent
+/* A request above one chunk takes a run of run_chunks(c) contiguous chunks
+ * from its class queue, which holds the first chunks of free runs in the
+ * order they were freed.  An empty queue is refilled with a run cut at the
+ * bump pointer, the only place where contiguous chunks are sure to be free
+ * (pooled chunks are not gathered into runs).  Reading: the paper is silent
  * on requests larger than a chunk. */
+static int run_carve(orc_heap *h, int c) {
+  uint64_t k = run_chunks(h, c);
+  if (virt(h) && seg_ensure(h, c, h->qtail[c])) return -1;   /* queue storage first */
+  if (h->bump + k > h->n_chunks) return -1;
+  uint64_t x = h->bump;
+  h->bump += k;
+  h->chunk_cls[x] = (int16_t)(CLS_RUN_FREE + c);
+  for (uint64_t i = 1; i < k; i++) h->chunk_cls[x + i] = (int16_t)(CLS_RUN_BODY + c);
+  h->carves[c] += k;
+  h->carved_now[c] += k;
+  q_push(h, c, x);
+  return 0;
+}
+
 static int64_t run_malloc(orc_heap *h, int c) {
-  uint64_t k = run_chunks(h, c), x;
-  if (h->runs[c].n) {
-    x = fifo_pop_back(&h->runs[c]);
-  } else {
-    if (h->bump + k > h->n_chunks) { h->failed[c]++; return -1; }
-    x = h->bump;
-    h->bump += k;
-    for (uint64_t i = 1; i < k; i++) h->chunk_cls[x + i] = (int16_t)(CLS_RUN_BODY + c);
-    h->carves[c] += k;
-    h->carved_now[c] += k;
-  }
+  if (h->q[c].n == 0 && run_carve(h, c)) { h->failed[c]++; return -1; }
+  uint64_t x = q_pop(h, c);
   h->chunk_cls[x] = (int16_t)c;
   uint64_t off = x * h->chunk_bytes;
   live_set(h, off, 1);
@@ -331,7 +336,7 @@ uint32_t orc_free(orc_heap *h, int64_t off_s) {
     live_set(h, off, 0);
     h->frees[c]++;
     h->chunk_cls[x] = (int16_t)(CLS_RUN_FREE + c);
-    fifo_push(&h->runs[c], x);
+    q_push(h, c, x);
     return 0;
   }
   uint64_t pb = orc_page_bytes(c);
@@ -401,18 +406,18 @@ void orc_trim(orc_heap *h) {
   if (!page_variant(h))
     for (uint64_t x = 0; x < h->n_chunks; x++)
       if (reclaim[x]) memset(h->bits + x * h->words_per_chunk, 0, h->words_per_chunk * 8);
-  /* 3b. every chunk of every free run goes back to the pool too */
+  /* 3b. every chunk of every free run (its class queue) goes back to the pool too */
   for (int c = h->n_classes; c < ORC_MAX_CLASSES; c++) {
     uint64_t k = run_chunks(h, c);
-    for (uint64_t i = 0; i < h->runs[c].n; i++) {
-      uint64_t x = fifo_at(&h->runs[c], i);
+    for (uint64_t i = 0; i < h->q[c].n; i++) {
+      uint64_t x = fifo_at(&h->q[c], i);
       for (uint64_t j = 0; j < k; j++) {
         h->chunk_cls[x + j] = CLS_NONE;
         fifo_push(&h->pool, x + j);
       }
       h->carved_now[c] -= k;
     }
-    fifo_clear(&h->runs[c]);
+    fifo_clear(&h->q[c]);
   }
   /* 4. canonical pool: ascending ids; lower the bump pointer over pooled chunks */
   uint64_t np = h->pool.n;
@@ -425,7 +430,7 @@ void orc_trim(orc_heap *h) {
   free(pv);
   /* 5. virtualized queues are re-laid from position 0, class by class */
   if (virt(h)) {
-    for (int c = 0; c < h->n_classes; c++) {
+    for (int c = 0; c < ORC_MAX_CLASSES; c++) {
       fifo items = h->q[c];
       memset(&h->q[c], 0, sizeof(fifo));
       fifo_clear(&h->segs[c]); fifo_clear(&h->spare[c]);
@@ -449,7 +454,7 @@ void orc_get_stats(const orc_heap *h, orc_stats *o) {
     o->failed[c] = h->failed[c];
     o->carves[c] = h->carves[c];
     o->carved_now[c] = h->carved_now[c];
-    o->queued[c] = c < h->n_classes ? h->q[c].n : h->runs[c].n;
+    o->queued[c] = h->q[c].n;
     o->live[c] = h->mallocs[c] - h->frees[c];
     o->seg_chunks += h->segs[c].n;
     o->spare_chunks += h->spare[c].n;
@@ -462,7 +467,7 @@ void orc_get_stats(const orc_heap *h, orc_stats *o) {
 }
 
 uint64_t orc_queue_items(const orc_heap *h, int c, uint64_t *out, uint64_t max) {
-  const fifo *f = c < h->n_classes ? &h->q[c] : &h->runs[c];   /* runs: free run starts */
+  const fifo *f = &h->q[c];   /* runs above one chunk: first chunks of free runs */
   for (uint64_t i = 0; i < f->n && i < max; i++) out[i] = fifo_at(f, i);
   return f->n;
 }

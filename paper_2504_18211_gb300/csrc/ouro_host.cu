@@ -73,7 +73,7 @@ __global__ void k_init_qhdr(ouro_heap_dev h) {
  * virtualized-array directory entry starts empty for segment index = entry */
 __global__ void k_init_cells(ouro_heap_dev h) {
   const unsigned item = ouro_qform((int)h.variant) == OURO_QF_VARRAY ? OURO_NIL : 0u;
-  for (int c = 0; c < (int)h.n_classes; ++c) {
+  for (int c = 0; c < OURO_MAX_CLASSES; ++c) {
     const unsigned long long R = h.ring_mask[c] + 1;
     unsigned long long *cells = h.cells + h.ring_off[c];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < R;
@@ -92,7 +92,7 @@ static ouro_status init_state(ouro_heap *H, cudaStream_t s) {
   ouro_heap_dev &d = H->d;
   OURO_CUDA(cudaMemsetAsync(H->meta + H->off_glob, 0, sizeof(ouro_glob), s));
   OURO_CUDA(cudaMemsetAsync(H->meta + H->off_stats, 0, H->stats_words * 8, s));
-  k_init_qhdr<<<d.n_classes, 128, 0, s>>>(d);
+  k_init_qhdr<<<OURO_MAX_CLASSES, 128, 0, s>>>(d);   /* every class, runs above one chunk too */
   OURO_LAUNCHED();
   const int grid = 4 * sm_count();
   k_fill_u8<<<grid, 256, 0, s>>>(d.chunk_cls, d.n_chunks, OURO_CLS_NONE);
@@ -171,17 +171,17 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
    * directory spans every position that can be live at once -- all items
    * of the class, plus waiting and in-flight positions -- in whole segments */
   unsigned long long ring_total = 0;
-  for (unsigned c = 0; c < d.n_classes; ++c) {
+  for (unsigned c = 0; c < OURO_MAX_CLASSES; ++c) {
     unsigned long long cap = 0, R = 0;
-    if (variant == OURO_PAGE_ARRAY) {
-      cap = bytes >> (4 + c);
-      if (cap > o.array_queue_capacity) cap = o.array_queue_capacity;
-      R = next_pow2(cap + OURO_RING_SLACK);
-    } else if (variant == OURO_CHUNK_ARRAY) {
-      cap = d.n_chunks;
+    /* items the class can ever hold: pages, chunk ids, or (above one chunk) runs */
+    const unsigned long long items = c >= d.n_classes ? d.n_chunks >> (c - d.n_classes + 1)
+                                     : is_page(variant) ? bytes >> (4 + c) : d.n_chunks;
+    if (variant == OURO_PAGE_ARRAY || variant == OURO_CHUNK_ARRAY) {
+      cap = items;
+      if (variant == OURO_PAGE_ARRAY && c < d.n_classes && cap > o.array_queue_capacity)
+        cap = o.array_queue_capacity;
       R = next_pow2(cap + OURO_RING_SLACK);
     } else if (is_varray(variant)) {
-      const unsigned long long items = is_page(variant) ? bytes >> (4 + c) : d.n_chunks;
       R = next_pow2((items + OURO_VA_SLACK + d.seg_cap - 1) / d.seg_cap + 4);
     }
     d.qcap[c] = cap;
@@ -195,7 +195,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   const bool need_free = !is_page(variant);
   const bool need_bits = !is_page(variant) || o.checked;
   size_t off = 0;
-  H->off_qhdr = off;  off = align256(off + sizeof(ouro_qhdr) * d.n_classes);
+  H->off_qhdr = off;  off = align256(off + sizeof(ouro_qhdr) * OURO_MAX_CLASSES);
   H->off_glob = off;  off = align256(off + sizeof(ouro_glob));
   H->stats_words = (size_t)(OURO_MAX_CLASSES + 1) * OURO_NSTAT * OURO_SHARDS;   /* + row OURO_ROW_NONE */
   H->off_stats = off; off = align256(off + H->stats_words * 8);
@@ -323,7 +323,7 @@ __global__ void k_chunk_hist(ouro_heap_dev h, unsigned long long *out) {
 /* segments on each class spare stack (quiescent) */
 __global__ void k_count_spares(ouro_heap_dev h, unsigned long long *out) {
   if (threadIdx.x) return;
-  for (unsigned c = 0; c < h.n_classes; ++c) {
+  for (unsigned c = 0; c < OURO_MAX_CLASSES; ++c) {
     unsigned x = lo32(qh(h, c)->spare.v);
     unsigned long long n = 0;
     while (x != OURO_NIL && n < h.n_chunks) {
@@ -334,30 +334,6 @@ __global__ void k_count_spares(ouro_heap_dev h, unsigned long long *out) {
   }
 }
 
-/* free runs on the stack of class c (quiescent); with out_ids, their first
- * chunks in stack order (at most cap) */
-__device__ unsigned long long walk_runs(const ouro_heap_dev &h, unsigned c, unsigned *out_ids,
-                                        unsigned long long cap) {
-  unsigned x1 = lo32(gl(h)->run_top[c].v);
-  unsigned long long n = 0;
-  while (x1 && n < h.n_chunks) {
-    if (out_ids && n < cap) out_ids[n] = x1 - 1;
-    n++;
-    x1 = *reinterpret_cast<const unsigned *>(h.base + ((size_t)(x1 - 1) << h.log2_chunk));
-  }
-  return n;
-}
-
-/* free runs per class above one chunk, into out[c] (quiescent) */
-__global__ void k_count_runs(ouro_heap_dev h, unsigned long long *out) {
-  for (unsigned c = h.n_classes + threadIdx.x; c < OURO_MAX_CLASSES; c += blockDim.x)
-    out[c] = walk_runs(h, c, nullptr, 0);
-}
-
-__global__ void k_collect_runs(ouro_heap_dev h, int c, unsigned *out, unsigned long long cap,
-                               unsigned long long *n_out) {
-  if (threadIdx.x == 0) *n_out = walk_runs(h, (unsigned)c, out, cap);
-}
 
 struct scratch_buf {
   void *p = nullptr;
@@ -380,7 +356,7 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
   unsigned long long *dq = (unsigned long long *)tmp.p, *dh = dq + (OURO_MAX_CLASSES + 1),
                      *ds = dh + (OURO_MAX_CLASSES + 1);
   OURO_CUDA(cudaMemsetAsync(tmp.p, 0, nt * 8, s));
-  k_count_queued<<<d.n_classes, 256, 0, s>>>(d, dq);
+  k_count_queued<<<OURO_MAX_CLASSES, 256, 0, s>>>(d, dq);
   OURO_LAUNCHED();
   k_chunk_hist<<<2 * sm_count(), 256, 0, s>>>(d, dh);
   OURO_LAUNCHED();
@@ -388,8 +364,6 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
     k_count_spares<<<1, 32, 0, s>>>(d, ds);
     OURO_LAUNCHED();
   }
-  k_count_runs<<<1, 32, 0, s>>>(d, dq);   /* rows n_classes.. of the queued counts */
-  OURO_LAUNCHED();
   std::vector<unsigned long long> hq(nt);
   OURO_CUDA(cudaMemcpyAsync(hq.data(), tmp.p, nt * 8, cudaMemcpyDeviceToHost, s));
   OURO_CUDA(cudaMemcpyAsync(st.data(), d.stats, H->stats_words * 8, cudaMemcpyDeviceToHost, s));
@@ -411,7 +385,7 @@ extern "C" ouro_status ouro_heap_stats(ouro_heap *H, ouro_stats *out, void *stre
     out->live[c] = out->mallocs[c] - out->frees[c];
     out->queued[c] = hq[c];
     out->carved_now[c] = hq[(OURO_MAX_CLASSES + 1) + c];
-    if (c < d.n_classes) out->spare_chunks += hq[2 * (OURO_MAX_CLASSES + 1) + c];
+    out->spare_chunks += hq[2 * (OURO_MAX_CLASSES + 1) + c];
   }
   out->seg_chunks = hq[(OURO_MAX_CLASSES + 1) + OURO_MAX_CLASSES];
   if (out->seg_chunks >= out->spare_chunks) out->seg_chunks -= out->spare_chunks;
@@ -451,7 +425,7 @@ extern "C" ouro_status ouro_heap_snapshot(ouro_heap *H, ouro_snapshot *out, void
   }
   scratch_buf cnt;
   OURO_CUDA(cudaMalloc(&cnt.p, 8));
-  for (unsigned c = 0; c < d.n_classes; ++c) {
+  for (unsigned c = 0; c < OURO_MAX_CLASSES; ++c) {   /* runs above one chunk: first chunks of free runs */
     ouro_qhdr hq;
     OURO_CUDA(cudaMemcpyAsync(&hq, qh(d, c), sizeof(hq), cudaMemcpyDeviceToHost, s));
     OURO_CUDA(cudaStreamSynchronize(s));
@@ -470,23 +444,7 @@ extern "C" ouro_status ouro_heap_snapshot(ouro_heap *H, ouro_snapshot *out, void
     if (n) OURO_CUDA(cudaMemcpyAsync(out->queue[c], items.p, n * 4, cudaMemcpyDeviceToHost, s));
     OURO_CUDA(cudaStreamSynchronize(s));
   }
-  /* classes above one chunk: their free runs (first chunks), stack order */
-  for (unsigned c = d.n_classes; c < OURO_MAX_CLASSES; ++c) {
-    const unsigned long long cap = d.n_chunks;
-    scratch_buf items;
-    OURO_CUDA(cudaMalloc(&items.p, cap * 4));
-    k_collect_runs<<<1, 32, 0, s>>>(d, (int)c, (unsigned *)items.p, cap, (unsigned long long *)cnt.p);
-    OURO_LAUNCHED();
-    unsigned long long n = 0;
-    OURO_CUDA(cudaMemcpyAsync(&n, cnt.p, 8, cudaMemcpyDeviceToHost, s));
-    OURO_CUDA(cudaStreamSynchronize(s));
-    if (n > cap) n = cap;
-    out->queue_n[c] = n;
-    out->queue[c] = (uint32_t *)malloc((n ? n : 1) * 4);
-    if (!out->queue[c]) return OURO_ENOMEM;
-    if (n) OURO_CUDA(cudaMemcpyAsync(out->queue[c], items.p, n * 4, cudaMemcpyDeviceToHost, s));
-    OURO_CUDA(cudaStreamSynchronize(s));
-  }
+
   return OURO_OK;
 }
 
@@ -550,24 +508,25 @@ __global__ void k_trim_old_pool(ouro_heap_dev h, unsigned char *in_pool) {
     in_pool[h.pool[i]] = 1;
 }
 
-/* free runs: every chunk of every run on a class stack joins the pool; the
- * stacks empty (one thread per class above one chunk) */
+/* free runs: every chunk of every run queued in a class above one chunk
+ * joins the pool (the queues are reset afterwards); blockIdx.y = class -
+ * n_classes */
 __global__ void k_trim_runs(ouro_heap_dev h, unsigned char *in_pool) {
-  for (unsigned c = h.n_classes + threadIdx.x; c < OURO_MAX_CLASSES; c += blockDim.x) {
-    const unsigned long long k = 1ull << (c - h.n_classes + 1);
-    unsigned long long *top = &gl(h)->run_top[c].v;
-    unsigned x1 = lo32(*top);
-    unsigned long long n = 0;
-    while (x1 && n < h.n_chunks) {
-      const unsigned x = x1 - 1;
-      x1 = *reinterpret_cast<const unsigned *>(h.base + ((size_t)x << h.log2_chunk));
-      for (unsigned long long i = 0; i < k; ++i) {
-        h.chunk_cls[x + i] = OURO_CLS_NONE;
-        in_pool[x + i] = 1;
-      }
-      n++;
+  const unsigned c = h.n_classes + blockIdx.y;
+  ouro_qhdr *q = qh(h, c);
+  const unsigned long long hd = q->head.v, tl = q->tail.v;
+  const unsigned long long k = 1ull << (c - h.n_classes + 1);
+  for (unsigned long long p = hd + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < tl;
+       p += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long *cell = slot_any(h, (int)c, p);
+    if (!cell) continue;
+    const unsigned long long v = *cell;
+    if (slot_d(v, p) != 1) continue;
+    const unsigned x = lo32(v);
+    for (unsigned long long i = 0; i < k; ++i) {
+      h.chunk_cls[x + i] = OURO_CLS_NONE;
+      in_pool[x + i] = 1;
     }
-    *top = pack(hi32(*top) + 1, 0u);
   }
 }
 
@@ -678,7 +637,7 @@ __global__ void k_trim_reset_q(ouro_heap_dev h, int c, const unsigned long long 
 
 /* chunks each class owns after the trim (from the chunk histogram) */
 __global__ void k_trim_carved(ouro_heap_dev h, const unsigned long long *hist) {
-  for (unsigned c = threadIdx.x; c < h.n_classes; c += blockDim.x) qh(h, c)->carved.v = hist[c];
+  for (unsigned c = threadIdx.x; c < OURO_MAX_CLASSES; c += blockDim.x) qh(h, c)->carved.v = hist[c];
 }
 
 /* virtualized-array directory: every entry empty for its own index */
@@ -742,7 +701,7 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   /* largest queue span decides the temp size */
   unsigned long long span_max = 1;
   std::vector<unsigned long long> spans(d.n_classes);
-  for (unsigned c = 0; c < d.n_classes; ++c) {
+  for (unsigned c = 0; c < d.n_classes; ++c) {        /* classes within a chunk keep their live pages */
     ouro_qhdr hq;
     OURO_CUDA(cudaMemcpy(&hq, qh(d, c), sizeof(hq), cudaMemcpyDeviceToHost));
     spans[c] = hq.tail.v > hq.head.v ? hq.tail.v - hq.head.v : 0;
@@ -752,9 +711,10 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   OURO_CUDA(cudaMalloc(&qcount.p, d.n_chunks * 4));
   OURO_CUDA(cudaMalloc(&in_pool.p, d.n_chunks));
   OURO_CUDA(cudaMalloc(&tmp.p, span_max * 4 * d.n_classes));
-  const size_t nwords = d.n_classes + 1 + OURO_MAX_CLASSES + 1;
+  const size_t nwords = OURO_MAX_CLASSES + 1 + OURO_MAX_CLASSES + 1;
   OURO_CUDA(cudaMalloc(&nbuf.p, 8 * nwords));
-  unsigned long long *ncount = (unsigned long long *)nbuf.p, *top = ncount + d.n_classes,
+  /* ncount: items each class keeps (0 for the run classes: all their queued runs are free) */
+  unsigned long long *ncount = (unsigned long long *)nbuf.p, *top = ncount + OURO_MAX_CLASSES,
                      *hist = top + 1;
   OURO_CUDA(cudaMemsetAsync(qcount.p, 0, d.n_chunks * 4, s));
   OURO_CUDA(cudaMemsetAsync(nbuf.p, 0, 8 * nwords, s));
@@ -765,8 +725,10 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   OURO_LAUNCHED();
   k_trim_old_pool<<<grid, 256, 0, s>>>(d, (unsigned char *)in_pool.p);
   OURO_LAUNCHED();
-  k_trim_runs<<<1, 32, 0, s>>>(d, (unsigned char *)in_pool.p);
-  OURO_LAUNCHED();
+  if (d.n_classes < OURO_MAX_CLASSES) {
+    k_trim_runs<<<dim3(grid, OURO_MAX_CLASSES - d.n_classes), 256, 0, s>>>(d, (unsigned char *)in_pool.p);
+    OURO_LAUNCHED();
+  }
   for (unsigned c = 0; c < d.n_classes; ++c) {
     k_trim_compact<<<1, 1024, 0, s>>>(d, (int)c, (const unsigned char *)in_pool.p,
                                       (unsigned *)tmp.p + (size_t)c * span_max, ncount + c);
@@ -776,8 +738,8 @@ extern "C" ouro_status ouro_heap_trim(ouro_heap *H, void *stream) {
   OURO_LAUNCHED();
   k_trim_pool<<<1, 1024, 0, s>>>(d, (const unsigned char *)in_pool.p, top);
   OURO_LAUNCHED();
-  for (unsigned c = 0; c < d.n_classes; ++c) {
-    const unsigned *src = (const unsigned *)tmp.p + (size_t)c * span_max;
+  for (unsigned c = 0; c < OURO_MAX_CLASSES; ++c) {
+    const unsigned *src = (const unsigned *)tmp.p + (size_t)(c < d.n_classes ? c : 0) * span_max;
     if (d.variant == OURO_PAGE_ARRAY || d.variant == OURO_CHUNK_ARRAY) {
       k_trim_relay_ring<<<grid, 256, 0, s>>>(d, (int)c, src, ncount + c);
       OURO_LAUNCHED();
@@ -876,7 +838,7 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
   OURO_CUDA(cudaMemsetAsync(scratch, 0, OURO_STATIC_SCRATCH_WORDS * 8, s));
   k_sum_shards<<<1, 256, 0, s>>>(d, dsum);
   OURO_LAUNCHED();
-  k_count_queued<<<d.n_classes, 256, 0, s>>>(d, dq);
+  k_count_queued<<<OURO_MAX_CLASSES, 256, 0, s>>>(d, dq);
   OURO_LAUNCHED();
   k_chunk_hist<<<2 * sm_count(), 256, 0, s>>>(d, dh);
   OURO_LAUNCHED();
@@ -884,8 +846,6 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
     k_count_spares<<<1, 32, 0, s>>>(d, ds);
     OURO_LAUNCHED();
   }
-  k_count_runs<<<1, 32, 0, s>>>(d, dq);
-  OURO_LAUNCHED();
   unsigned long long hv[OURO_STATIC_SCRATCH_WORDS];
   ouro_glob g;
   OURO_CUDA(cudaMemcpyAsync(hv, scratch, sizeof(hv), cudaMemcpyDeviceToHost, s));
@@ -906,7 +866,7 @@ extern "C" ouro_status ouro_heap_stats_static(ouro_heap *H, ouro_stats *out, voi
     out->live[c] = out->mallocs[c] - out->frees[c];
     out->queued[c] = hq[c];
     out->carved_now[c] = hh[c];
-    if (c < d.n_classes) out->spare_chunks += hsp[c];
+    out->spare_chunks += hsp[c];
   }
   out->seg_chunks = hh[OURO_MAX_CLASSES];
   if (out->seg_chunks >= out->spare_chunks) out->seg_chunks -= out->spare_chunks;

@@ -15,19 +15,11 @@ namespace detail {
 template <int V>
 __device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long long n, bool want = true) {
   const unsigned mask = __activemask();
-  int cls = want ? size_class(h, n) : -1;
+  const int cls = want ? size_class(h, n) : -1;
   if (want && cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
-  void *run = nullptr;
-  const bool is_run = cls >= (int)h.n_classes;
-  if (is_run) {                       /* above one chunk: a run, then help the others */
-    run = run_malloc(h, cls);
-    cls = -1;
-  }
-  if (!__any_sync(mask, cls >= 0)) return run;
-  void *r;
-  if constexpr (ouro_page_queues(V)) r = page_malloc<V>(h, cls, mask);
-  else r = chunk_malloc<V>(h, cls, mask);
-  return is_run ? run : r;
+  if (!__any_sync(mask, cls >= 0)) return nullptr;
+  if constexpr (ouro_page_queues(V)) return page_malloc<V>(h, cls, mask);   /* pages and runs */
+  else return chunk_or_run_malloc<V>(h, cls, mask);
 }
 
 template <int V>
@@ -39,8 +31,7 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (cls >= (int)h.n_classes) {   /* a run */
-      run_free(h, cls, item);
-      cls = -1;
+      if (!run_mark_free(h, cls, item)) cls = -1;
     } else if (h.checked && ouro_page_queues(V)) {
       const unsigned sh = h.log2_chunk - 4 - cls;
       const unsigned pg = item & ((1u << sh) - 1), x = item >> sh, bit = 1u << (pg & 31);
@@ -53,7 +44,7 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
     }
   }
   if constexpr (!ouro_page_queues(V)) {
-    chunk_free_impl<V>(h, cls, p, mask);
+    chunk_or_run_free<V>(h, cls, item, p, mask);
   } else {
     const unsigned vmask = __ballot_sync(mask, cls >= 0);
     if (cls < 0) return;

@@ -102,14 +102,15 @@ def pin_capacity(lib_path):
         assert got == (qc // 64) * 64, (cap, got)
     # runs above one chunk: 3000 B on 1 KiB chunks is a 4 KiB run of 4 chunks
     # (class 8); 64 chunks hold floor(64 / 4) = 16 runs, each at the next bump
-    # position; freed runs are reused (last freed first) without moving the bump
-    for variant in ALL_VARIANTS:
+    # position; freed runs are reused in the order they were freed, without
+    # moving the bump (plain array queues: the heap holds no queue segments)
+    for variant in ("page_array", "chunk_array"):
         h = heap(lib_path, 64 * 1024, 1024, variant)
         offs = [h.malloc(3000) for _ in range(20)]
         assert offs[:16] == [4096 * i for i in range(16)] and offs[16:] == [-1] * 4, (variant, offs)
         st = h.stats()
         assert st["mallocs"][8] == 16 and st["failed"][8] == 4 and st["carved_now"][8] == 64, (variant, st)
-        for o in offs[:16]:
+        for o in offs[15::-1]:
             assert h.free(o) == 0
         assert h.free(offs[3]) == oracle.ERR_DOUBLE_FREE and h.free(offs[3] + 1024) == oracle.ERR_BAD_FREE
         again = [h.malloc(2049) for _ in range(16)]         # 2049 B: the same class

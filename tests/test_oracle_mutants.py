@@ -37,8 +37,9 @@ MUTANTS = {
     "trim_reclaims_partial": ("if (fr == ppc) reclaim[x] = 1;", "if (fr + 1 >= ppc) reclaim[x] = 1;"),
     "chunk_full_not_popped": ("if (h->free_pages[x] == 0) q_pop(h, c);", ""),
     "fmix_shift": ("x ^= x >> 13;", "x ^= x >> 12;"),
-    "free_run_not_reused": ("  if (h->runs[c].n) {", "  if (0) {"),
-    "run_overlaps_next": ("    h->bump += k;", "    h->bump += 1;"),
+    "free_run_not_reused": ("  if (h->q[c].n == 0 && run_carve(h, c)) { h->failed[c]++; return -1; }",
+                            "  if (run_carve(h, c)) { h->failed[c]++; return -1; }"),
+    "run_overlaps_next": ("  h->bump += k;", "  h->bump += 1;"),
     "trim_keeps_free_runs": ("        h->chunk_cls[x + j] = CLS_NONE;", ""),
     "run_double_free_missed": ("    if (c >= CLS_RUN_FREE) { h->err |= ORC_ERR_DOUBLE_FREE; return ORC_ERR_DOUBLE_FREE; }", ""),
 }
