@@ -31,15 +31,17 @@ def ouro():
 
 @pytest.mark.parametrize("variant", ALL_VARIANTS)
 def test_run_fill_reuse_and_bad_frees(ouro, variant):
-    """64 chunks of 8 KiB; 20000 B is class 11, a run of 4 chunks: exactly
-    16 of 20 requests succeed, as in the oracle; after freeing them all, 16
-    requests of the same class reuse the runs without moving the bump."""
+    """64 chunks of 8 KiB; 20000 B is class 11, a run of 4 chunks.  Exactly
+    as many of 20 requests succeed as in the oracle (16; 15 with virtualized
+    queues, whose first segment takes a chunk); after freeing them all, as
+    many requests of the same class reuse the runs without moving the bump."""
     torch = torch_cuda()
     bytes_, chunk, size = 64 * 8192, 8192, 20000
     sizes = W.single_size(20, size)
     oh = oracle.OracleHeap(bytes_, chunk, variant)
     o_ok = sum(1 for _ in range(20) if oh.malloc(size) >= 0)
-    assert o_ok == 16
+    assert o_ok == (16 if variant in ("page_array", "chunk_array") else 15)
+    ost = oh.stats()
     with ouro.Heap(bytes_, chunk, variant) as heap:
         ptrs = heap.malloc(to_dev(sizes))
         torch.cuda.synchronize()
@@ -47,18 +49,18 @@ def test_run_fill_reuse_and_bad_frees(ouro, variant):
         assert int((p != 0).sum()) == o_ok
         assert_no_overlap(p, sizes, heap.base, bytes_, chunk)
         st = heap.stats()
-        assert st["n_large"] == 7 and st["mallocs"][11] == 16 and st["failed"][11] == 4
-        assert st["carved_now"][11] == 64 and st["bump"] == 64
+        assert st["n_large"] == 7 and st["mallocs"][11] == o_ok and st["failed"][11] == 20 - o_ok
+        assert st["carved_now"][11] == ost["carved_now"][11] == 4 * o_ok and st["bump"] == ost["bump"]
         live = ptrs[p != 0].clone()
         heap.free(live)
         torch.cuda.synchronize()
-        assert heap.stats()["queued"][11] == 16
-        again = heap.malloc(to_dev(W.single_size(16, 16385)))     # same class, smaller size
+        assert heap.stats()["queued"][11] == o_ok
+        again = heap.malloc(to_dev(W.single_size(o_ok, 16385)))  # same class, smaller size
         torch.cuda.synchronize()
         a = again.cpu().numpy().view(np.uint64)
         assert np.array_equal(np.sort(a), np.sort(p[p != 0]))     # the very same runs
         st = heap.stats()
-        assert st["bump"] == 64 and st["carves"][11] == 64 and st["error_bits"] == 0
+        assert st["bump"] == ost["bump"] and st["carves"][11] == 4 * o_ok and st["error_bits"] == 0
         heap.free(again[:1].clone())
         heap.free(again[:1].clone())                             # double free of a run
         inner = torch.from_numpy(np.array([int(a[1]) + chunk], np.int64)).cuda()
@@ -66,7 +68,7 @@ def test_run_fill_reuse_and_bad_frees(ouro, variant):
         torch.cuda.synchronize()
         st = heap.stats()
         assert st["error_bits"] & ouro.B.ERR_DOUBLE_FREE and st["error_bits"] & ouro.B.ERR_BAD_FREE
-        assert st["frees"][11] == 16 + 1
+        assert st["frees"][11] == o_ok + 1
         heap.free(again[1:].clone())
         heap.reset()
 
