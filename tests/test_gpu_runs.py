@@ -2,11 +2,12 @@
 
 The paper is silent on requests larger than a chunk; both implementations
 read them as runs of 2^(c - n_classes + 1) chunks for class c, cut at the
-bump pointer, reused from a per-class stack after a free, and returned to the
+bump pointer, reused from the class queue after a free, and returned to the
 pool by trim.  Compared with the oracle: successes and nulls of a fill
-(exact: runs are cut one request at a time), counts and read-back checksums
-of rounds that mix pages and runs, reuse without new carving, double frees
-and frees inside a run, and the post-create state after free-all + trim.
+(exact: a run class carves only for the debt it has), counts and read-back
+checksums of rounds that mix pages and runs, reuse without new carving,
+double frees and frees inside a run, and the post-create state after
+free-all + trim.
 """
 import numpy as np
 import pytest
