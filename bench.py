@@ -76,8 +76,8 @@ def dist_env():
 # from the sources whose digest is recorded; null once they change.
 FUSED_KERNEL_SOURCES = ("include/ouro_device.cuh", "paper_2504_18211_gb300/csrc/ouro_payload.cuh",
                         "paper_2504_18211_gb300/csrc/ouro_kernels.cu", "paper_2504_18211_gb300/csrc/ouro_internal.cuh")
-FUSED_TRAFFIC = {"sources_sha256": "25c47d941b099e8d0537e384700b0714e513d727c85ceee51ec0f71958f4a58d",
-                 "bytes_per_launch": 1632661760}
+FUSED_TRAFFIC = {"sources_sha256": "403547d0b8a3d557af873fa0246fe4d5026a91cab9efc6e74c5da65095b3c33e",
+                 "bytes_per_launch": 1659415296}
 
 
 def kernel_sources_digest() -> str:
