@@ -52,8 +52,11 @@ __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, ui
  * uneven sizes balance across warps and the round ends within one task of
  * the last byte.  STAGE: the warp's freed pages serve its next mallocs of
  * the same class from shared memory (page queues, heap option `staging`). */
+#ifndef OURO_FUSED_MIN_BLOCKS
+#define OURO_FUSED_MIN_BLOCKS 4   /* resident blocks of 256 per SM the fused round is compiled for */
+#endif
 template <int V, bool STAGE>
-__global__ void __launch_bounds__(256, 4) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
+__global__ void __launch_bounds__(256, OURO_FUSED_MIN_BLOCKS) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
                                                      uint32_t seed, int mode, ouro_check *out, void **ptrs,
                                                      unsigned long long *work) {
   __shared__ ouro_block_ctx<8> ctx;
