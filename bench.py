@@ -57,9 +57,10 @@ def parse():
     ap.add_argument("--form", choices=("fused", "per_launch"), default="fused",
                     help="fused: one kernel per round; per_launch: malloc / write / check / free kernels")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", choices=("sweep", "batching", "serving", "graph"), default="sweep",
+    ap.add_argument("--workload", choices=("sweep", "batching", "serving", "graph", "axes"), default="sweep",
                     help="sweep: the headline size sweep; batching: 256 uneven batches, every form + autotuner; "
-                         "serving: the device request loop")
+                         "serving: the device request loop; graph: adjacency-list growth; axes: the paper's "
+                         "allocation-size and thread-count axes on all six queue forms")
     ap.add_argument("--batches", type=int, default=256)
     return ap.parse_args()
 
@@ -402,10 +403,70 @@ def run_graph(args):
     print(json.dumps(res))
 
 
+def run_axes(args):
+    """The paper's experiment axes (Sec. 4.1-4.3): average time of the
+    allocation kernel and of the free kernel (a) over allocation sizes
+    16 B .. 8 KiB at 1024 threads and (b) over 2^5 .. 2^20 threads at 1000 B,
+    each point ten iterations of allocate / write / check / free after one
+    untimed iteration (the paper's subsequent-iteration average, Sec. 3), on
+    all six queue forms; 1 GiB heap of 8 KiB chunks."""
+    import numpy as np
+    import torch
+
+    import paper_2504_18211_gb300 as P
+    from paper_2504_18211_gb300 import build as B
+    from paper_2504_18211_gb300 import workloads as W
+    B.build()
+    P.load()
+    stream = torch.cuda.current_stream()
+    variants = ("page_array", "chunk_array", "page_varray", "page_vlist", "chunk_varray", "chunk_vlist")
+    axes = {"size": [(1024, 16 << k) for k in range(10)],
+            "threads": [(1 << k, 1000) for k in range(5, 21)]}
+    res = {"workload": "paper axes: allocation size x 1024 threads and thread count x 1000 B; 10 timed "
+                       "iterations after 1 untimed; 1 GiB heap, 8 KiB chunks", "unit": "us per kernel launch",
+           "variants": {}}
+    ok_all = True
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for v in variants:
+        out_v = {}
+        with P.Heap(1 << 30, 8192, v) as heap:
+            for axis, points in axes.items():
+                rows = []
+                for threads, size in points:
+                    sizes = torch.from_numpy(W.single_size(threads, size).view(np.int32)).cuda()
+                    ptrs = torch.empty(threads, dtype=torch.int64, device="cuda")
+                    chk = torch.zeros(5, dtype=torch.int64, device="cuda")
+                    t_m, t_f = [], []
+                    for it in range(11):
+                        ev[0].record(stream)
+                        heap.malloc(sizes, ptrs)
+                        ev[1].record(stream)
+                        P.pattern_write(ptrs, sizes, it, 1)
+                        P.pattern_check(ptrs, sizes, it, 1, chk)
+                        ev[2].record(stream)
+                        heap.free(ptrs)
+                        ev[3].record(stream)
+                        torch.cuda.synchronize()
+                        c = P.check_to_dict(chk)
+                        ok_all &= c["nulls"] == 0 and c["mismatches"] == 0
+                        if it:
+                            t_m.append(ev[0].elapsed_time(ev[1]) * 1e3)
+                            t_f.append(ev[2].elapsed_time(ev[3]) * 1e3)
+                    rows.append({"threads": threads, "size": size, "alloc_us": round(statistics.mean(t_m), 2),
+                                 "free_us": round(statistics.mean(t_f), 2)})
+                out_v[axis] = rows
+            ok_all &= heap.stats()["error_bits"] == 0
+        res["variants"][v] = out_v
+    res["verified"] = bool(ok_all)
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "axes":
+        return run_axes(args)
     if args.workload == "batching":
         return run_batching(args)
     if args.workload == "serving":
