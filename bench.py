@@ -62,6 +62,8 @@ def parse():
                          "serving: the device request loop; graph: adjacency-list growth; axes: the paper's "
                          "allocation-size and thread-count axes on all six queue forms")
     ap.add_argument("--batches", type=int, default=256)
+    ap.add_argument("--axes-point", default="",
+                    help="axes workload: one point THREADS,SIZE only (with --variant; used under a profiler)")
     return ap.parse_args()
 
 
@@ -425,6 +427,9 @@ def run_axes(args):
     variants = ("page_array", "chunk_array", "page_varray", "page_vlist", "chunk_varray", "chunk_vlist")
     axes = {"size": [(1024, 16 << k) for k in range(10)],
             "threads": [(1 << k, 1000) for k in range(5, 21)]}
+    if args.axes_point:
+        t, z = (int(x) for x in args.axes_point.split(","))
+        variants, axes = (args.variant,), {"point": [(t, z)]}
     res = {"workload": "paper axes: allocation size x 1024 threads and thread count x 1000 B; 10 timed "
                        "iterations after 1 untimed; 4 GiB heap, 8 KiB chunks, reset per point", "unit": "us per kernel launch",
            "variants": {}}
@@ -444,6 +449,9 @@ def run_axes(args):
                     chk = torch.zeros(5, dtype=torch.int64, device="cuda")
                     t_m, t_f = [], []
                     for it in range(11):
+                        # keep the GPU busy while the host queues the launches,
+                        # so the events time the kernels and not host gaps
+                        torch.cuda._sleep(2_000_000)
                         ev[0].record(stream)
                         heap.malloc(sizes, ptrs)
                         ev[1].record(stream)
