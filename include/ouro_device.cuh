@@ -349,10 +349,14 @@ __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) 
 
 /* A retired list segment x is appended behind the back segment (ahead of
  * the producers, at most OURO_AHEAD_POS positions past the tail), so that
- * producers find their segments linked; else it joins the spare stack. */
+ * producers find their segments linked; else it joins the spare stack.
+ * Appends are serial (each needs the previous link), so when many segments
+ * retire at once most of them land on the spare stack: the thread that
+ * wins an append keeps appending from the spare stack behind its own
+ * segment while no other thread is appending. */
 __device__ inline void vl_recycle(const ouro_heap_dev &h, int c, unsigned x) {
   ouro_qhdr *q = qh(h, c);
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < 8 && x != OURO_NIL; ++k) {
     const unsigned long long b = ld_acq(&q->back.v);
     const unsigned bx = lo32(b);
     if (bx >= OURO_BUSY) break;
@@ -370,9 +374,10 @@ __device__ inline void vl_recycle(const ouro_heap_dev &h, int c, unsigned x) {
     st_rel(&sg->link, pack(hi32(b), x));
     cas_ar(&q->back.v, b, pack(hi32(b) + 1, x));
     st_rlx(&q->hint[(hi32(b) + 1) & (OURO_VL_HINTS - 1)], pack(hi32(b) + 1, x));
-    return;
+    x = (lo32(ld_rlx(&q->spare.v)) != OURO_NIL) ? spare_pop(h, c) : OURO_NIL;   /* go on with a spare */
+    k = -1;
   }
-  spare_push(h, c, x);
+  if (x != OURO_NIL) spare_push(h, c, x);
 }
 
 /* Retire fully used front segments (all slots produced and consumed, and a
@@ -405,12 +410,13 @@ __device__ __forceinline__ unsigned long long *va_entry(const ouro_heap_dev &h, 
 }
 
 /* Segment x has seen all its position events: its entry is emptied for the
- * next lap (index + D), and the chunk is set up again as the first missing
- * segment ahead of the producers (a burst of producers then finds its
- * segments in place); the class front line keeps (next index << 32) as the
- * place to look.  With no missing entry close enough ahead (within D/2
- * segments, or OURO_AHEAD_POS positions, of the tail) it joins the spare
- * stack. */
+ * next lap (index + D), and the chunk is set up again as a missing segment
+ * ahead of the producers, so that a burst of producers finds its segments in
+ * place.  The class front line counts out those indices, (next index << 32)
+ * | NIL: every retiring segment takes its own, starting past the tail's
+ * segment.  An index whose entry a producer has made meanwhile is skipped;
+ * past D/2 segments, or OURO_AHEAD_POS positions, ahead of the tail the
+ * chunk joins the spare stack instead. */
 __device__ inline void va_retire(const ouro_heap_dev &h, int c, unsigned x) {
   ouro_qhdr *q = qh(h, c);
   const unsigned idx = hi32(ld_acq(&seg_of(h, x)->link));
@@ -418,15 +424,19 @@ __device__ inline void va_retire(const ouro_heap_dev &h, int c, unsigned x) {
   st_rel(va_entry(h, c, idx), pack(idx + (unsigned)D, OURO_NIL));
   const unsigned long long tail = ld_rlx(&q->tail.v), ts = tail / h.seg_cap;
   const unsigned long long lim = ts + min(D >> 1, OURO_AHEAD_POS / h.seg_cap + 1);
-  unsigned long long sn = max(ts + 1, (unsigned long long)hi32(ld_rlx(&q->front.v)));
-  for (int k = 0; k < 8 && sn < lim; ++k, ++sn) {
+  for (int k = 0; k < 8; ++k) {
+    const unsigned long long sn = hi32(atomicAdd(&q->front.v, 1ull << 32));
+    if (sn < ts + 1) {                     /* the count fell behind the tail: jump past it */
+      atomicMax(&q->front.v, pack((unsigned)(ts + 1), OURO_NIL));
+      continue;
+    }
+    if (sn >= lim) break;
     unsigned long long *e = va_entry(h, c, sn);
     const unsigned long long v = pack((unsigned)sn, OURO_NIL);
     if (ld_rlx(e) != v) continue;
     if (cas_ar(e, v, pack((unsigned)sn, OURO_BUSY)) != v) continue;
     seg_init(h, x, (unsigned)sn, false);
     st_rel(e, pack((unsigned)sn, x));
-    atomicMax(&q->front.v, pack((unsigned)(sn + 1), OURO_NIL));
     return;
   }
   spare_push(h, c, x);
