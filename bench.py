@@ -431,7 +431,8 @@ def run_axes(args):
         t, z = (int(x) for x in args.axes_point.split(","))
         variants, axes = (args.variant,), {"point": [(t, z)]}
     res = {"workload": "paper axes: allocation size x 1024 threads and thread count x 1000 B; 10 timed "
-                       "iterations after 1 untimed; 4 GiB heap, 8 KiB chunks, reset per point", "unit": "us per kernel launch",
+                       "iterations after 1 untimed (median); 4 GiB heap, 8 KiB chunks, reset per point",
+           "unit": "us per kernel launch",
            "variants": {}}
     ok_all = True
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -467,8 +468,8 @@ def run_axes(args):
                             t_m.append(ev[0].elapsed_time(ev[1]) * 1e3)
                             t_f.append(ev[2].elapsed_time(ev[3]) * 1e3)
                     ok_all &= heap.stats()["error_bits"] == 0
-                    rows.append({"threads": threads, "size": size, "alloc_us": round(statistics.mean(t_m), 2),
-                                 "free_us": round(statistics.mean(t_f), 2)})
+                    rows.append({"threads": threads, "size": size, "alloc_us": round(statistics.median(t_m), 2),
+                                 "free_us": round(statistics.median(t_f), 2)})
                 out_v[axis] = rows
         res["variants"][v] = out_v
     res["verified"] = bool(ok_all)

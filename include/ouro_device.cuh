@@ -47,7 +47,7 @@
 #define OURO_CLS_RUN_BODY 0x80u   /* | class: second or later chunk of a run */
 #define OURO_MAX_REQUEST (16ull << (OURO_MAX_CLASSES - 1))   /* 1 MiB */
 #define OURO_ROW_NONE OURO_MAX_CLASSES   /* counter row of requests without a class */
-#define OURO_VL_HINTS 1024
+#define OURO_VL_HINTS 4096   /* lookaside hints per class: segments live at once in a burst of 2^22 positions */
 #define OURO_NSTAT 8
 #define OURO_SHARDS 32
 #define OURO_SEG_HDR 64
@@ -575,6 +575,15 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
   unsigned ns = h.backoff_min_ns;
   unsigned long long cur = 0;
   bool walking = false;
+  /* a missed hint: start from the nearest valid hint a few segments back */
+  for (unsigned k = 1; k <= 8 && k <= s32; ++k) {
+    const unsigned long long e2 = ld_rlx(&q->hint[(s32 - k) & (OURO_VL_HINTS - 1)]);
+    if (hi32(e2) == s32 - k && lo32(e2) < OURO_BUSY && hi32(ld_acq(&seg_of(h, lo32(e2))->link)) == s32 - k) {
+      cur = e2;
+      walking = true;
+      break;
+    }
+  }
   for (unsigned it = 0; it < h.spin_limit; ++it) {
     if (!walking) {
       cur = ld_acq(&q->back.v);
