@@ -300,9 +300,12 @@ ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
  *   d_tables n_slots*max_blocks pointers, d_sess_out 5*n_sessions words
  *   (xor, sum, mismatches, admit step, done step; all ones if never),
  *   d_step_ns 3*`steps` %globaltimer stamps (after admission, growth and
- *   completion of each step), d_ctl 9 words (barrier state, next
+ *   completion of each step), d_ctl 11 words (barrier state, next
  *   arrival, committed blocks, error flag, mallocs, frees, failed mallocs,
- *   free-slot stack top), d_free_stack n_slots slot ids.
+ *   free-slot stack top, sessions finished and free tasks taken in the
+ *   step), d_free_stack 2*n_slots slot ids (the free-slot stack, then the
+ *   step's list of finished sessions, whose blocks every warp helps free
+ *   in tasks of 256).
  * ENOTSUP if the device cannot launch cooperative kernels.  A grid barrier
  * whose wait runs out sets d_ctl[4] and ends the kernel. */
 ouro_status ouro_serve(ouro_heap *h, const uint32_t *d_arrive_step, const uint32_t *d_blocks, uint32_t n_sessions,

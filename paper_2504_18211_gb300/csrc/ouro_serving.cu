@@ -11,8 +11,11 @@
  *      ouro_malloc, records it in its block table, writes its pattern
  *      (seed + session id, block index) and reads it back through L2,
  *      folding the words into the session checksum;
- *   3. completion (all warps): a session that reached its size frees every
- *      block and reports its checksum; its slot is free for the next step.
+ *   3. completion: a session that reached its size reports its checksum and
+ *      its slot is free for the next step (one thread per slot); after a
+ *      barrier, every warp pulls tasks of 256 of the finished sessions'
+ *      blocks and frees them, so that one long session does not hold the
+ *      step for a single warp.
  * The allocator state, the session table and the block tables stay resident
  * for the whole run; requests that arrive while others are running are
  * admitted as slots and memory free up, and their work overlaps on the GPU.
@@ -43,8 +46,10 @@ struct serve_args {
   unsigned long long *step_ns;   /* per step: %globaltimer after admission, growth and completion (3 words) */
   unsigned long long *ctl;       /* [0] barrier count, [1] barrier generation, [2] next arrival,
                                     [3] committed blocks, [4] error, [5] mallocs, [6] frees, [7] failed,
-                                    [8] free-slot stack top */
+                                    [8] free-slot stack top, [9] sessions finished this step,
+                                    [10] free tasks handed out this step */
   uint32_t *free_stack;          /* free slot ids (stack of n_slots) */
+  uint32_t *done_list;           /* slots whose sessions finished this step (n_slots) */
   uint32_t steps;
   uint32_t seed;
   unsigned long long cap_blocks; /* admission cap */
@@ -122,6 +127,8 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
   for (uint32_t step = 0; step < A.steps; ++step) {
     /* 1. admission: arrival order, a free slot (stack), committed + newcomer <= cap */
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+      A.ctl[9] = 0;                       /* the previous step's free tasks are all done */
+      A.ctl[10] = 0;
       unsigned long long next = A.ctl[2], committed = A.ctl[3], top = A.ctl[8];
       while (next < A.n_sessions && A.arrive_step[next] <= step && committed + A.blocks[next] <= A.cap_blocks &&
              top > 0) {
@@ -171,28 +178,63 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[3 * step + 1] = globaltimer();
-    /* 3. completion: a warp per finished session frees its blocks */
-    for (uint32_t slot = warp; slot < A.n_slots; slot += nwarps) {
+    /* 3a. completion: a session that reached its size reports, releases its
+     *     slot (reused from the next step on) and is listed for freeing */
+    for (uint32_t slot = blockIdx.x * blockDim.x + threadIdx.x; slot < A.n_slots; slot += gridDim.x * blockDim.x) {
       const int sess = A.slot_session[slot];
       if (sess < 0 || A.slot_k[slot] < A.blocks[sess]) continue;
-      const uint32_t nb = A.slot_k[slot];
-      for (uint32_t b0 = 0; b0 < nb; b0 += 32) {
-        const uint32_t b = b0 + lane;
-        void *p = b < nb ? reinterpret_cast<void *>(A.tables[(size_t)slot * A.max_blocks + b]) : nullptr;
-        if (b < nb) free_v<V>(h, p);
-        __syncwarp();
+      A.sess_out[5 * sess + 0] = A.slot_acc[3 * slot];
+      A.sess_out[5 * sess + 1] = A.slot_acc[3 * slot + 1];
+      A.sess_out[5 * sess + 2] = A.slot_acc[3 * slot + 2];
+      A.sess_out[5 * sess + 4] = step;
+      atomicAdd(&A.ctl[6], (unsigned long long)A.slot_k[slot]);
+      atomicAdd(&A.ctl[3], 0ull - (unsigned long long)A.blocks[sess]);
+      A.slot_session[slot] = -1;
+      A.free_stack[atomicAdd(&A.ctl[8], 1ull)] = slot;
+      A.done_list[atomicAdd(&A.ctl[9], 1ull)] = slot;
+    }
+    if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
+    /* 3b. the listed sessions' blocks, in tasks of 256 blocks pulled by warps:
+     *     task c is piece c - (pieces of the earlier list entries) of the first
+     *     entry whose running piece count passes c */
+    {
+      const unsigned long long nl = *(volatile unsigned long long *)&A.ctl[9];
+      for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(&A.ctl[10], 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        unsigned long long before = 0;
+        uint32_t slot = 0, nb = 0;
+        bool found = false;
+        for (unsigned long long i0 = 0; i0 < nl && !found; i0 += 32) {
+          const unsigned long long i = i0 + lane;
+          const uint32_t s_i = i < nl ? A.done_list[i] : 0;
+          const uint32_t nb_i = i < nl ? A.slot_k[s_i] : 0;
+          unsigned long long pc = (nb_i + 255) / 256, incl = pc;
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((int)lane >= o) incl += y;
+          }
+          const unsigned hit = __ballot_sync(0xffffffffu, i < nl && before + incl > c);
+          if (hit) {
+            const int l = __ffs(hit) - 1;
+            slot = __shfl_sync(0xffffffffu, s_i, l);
+            nb = __shfl_sync(0xffffffffu, nb_i, l);
+            before += __shfl_sync(0xffffffffu, incl - pc, l);
+            found = true;
+          } else {
+            before += __shfl_sync(0xffffffffu, incl, 31);
+          }
+        }
+        if (!found) break;
+        const uint32_t b_lo = (uint32_t)(c - before) * 256, b_hi = min(nb, b_lo + 256);
+        for (uint32_t b0 = b_lo; b0 < b_hi; b0 += 32) {
+          const uint32_t b = b0 + lane;
+          void *p = b < b_hi ? reinterpret_cast<void *>(A.tables[(size_t)slot * A.max_blocks + b]) : nullptr;
+          if (b < b_hi) free_v<V>(h, p);
+          __syncwarp();
+        }
       }
-      if (lane == 0) {
-        atomicAdd(&A.ctl[6], (unsigned long long)nb);
-        A.sess_out[5 * sess + 0] = A.slot_acc[3 * slot];
-        A.sess_out[5 * sess + 1] = A.slot_acc[3 * slot + 1];
-        A.sess_out[5 * sess + 2] = A.slot_acc[3 * slot + 2];
-        A.sess_out[5 * sess + 4] = step;
-        atomicAdd(&A.ctl[3], 0ull - (unsigned long long)A.blocks[sess]);
-        A.slot_session[slot] = -1;
-        A.free_stack[atomicAdd(&A.ctl[8], 1ull)] = slot;
-      }
-      __syncwarp();
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) A.step_ns[3 * step + 2] = globaltimer();
@@ -215,7 +257,7 @@ extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, c
     return OURO_EINVAL;
   cudaStream_t s = S(stream);
   OURO_CUDA(cudaMemsetAsync(d_slot_session, 0xFF, n_slots * sizeof(int), s));
-  OURO_CUDA(cudaMemsetAsync(d_ctl, 0, 9 * 8, s));
+  OURO_CUDA(cudaMemsetAsync(d_ctl, 0, 11 * 8, s));
   OURO_CUDA(cudaMemsetAsync(d_sess_out, 0xFF, (size_t)n_sessions * 5 * 8, s));
   serve_args A;
   A.h = H->d;
@@ -232,6 +274,7 @@ extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, c
   A.step_ns = d_step_ns;
   A.ctl = d_ctl;
   A.free_stack = d_free_stack;
+  A.done_list = d_free_stack + n_slots;
   A.steps = steps;
   A.seed = seed;
   A.cap_blocks = cap_blocks;

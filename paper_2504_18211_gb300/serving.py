@@ -31,8 +31,8 @@ class ServeRun:
         self.tables = torch.empty(n_slots * max_blocks, dtype=torch.int64, device=dev)
         self.sess_out = torch.empty(5 * max(self.n, 1), dtype=torch.int64, device=dev)
         self.step_ns = torch.zeros(3 * steps, dtype=torch.int64, device=dev)
-        self.ctl = torch.zeros(9, dtype=torch.int64, device=dev)
-        self.free_stack = torch.empty(n_slots, dtype=torch.int32, device=dev)
+        self.ctl = torch.zeros(11, dtype=torch.int64, device=dev)
+        self.free_stack = torch.empty(2 * n_slots, dtype=torch.int32, device=dev)   # stack, then done list
 
     def run(self, heap, cap_blocks: int, blocks_per_sm: int = 0) -> float:
         """One call of the device loop; returns its duration in ms (CUDA events)."""
