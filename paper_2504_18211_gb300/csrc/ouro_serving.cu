@@ -3,10 +3,12 @@
  * persistent kernel for all steps) over sessions whose memory grows.
  *
  * Each step:
- *   1. admission (block 0, thread 0): sessions that have arrived are admitted
+ *   1. admission (block 0, warp 0): sessions that have arrived are admitted
  *      in arrival order while a session slot is free and the blocks committed
  *      to admitted sessions, plus the newcomer's total, stay within the
- *      admission cap (95 % of the heap's blocks);
+ *      admission cap (95 % of the heap's blocks); the warp weighs 32
+ *      arrivals at a time and admits the longest run of them, from the
+ *      first, that passes;
  *   2. growth (all warps): every active session allocates one block with
  *      ouro_malloc, records it in its block table, writes its pattern
  *      (seed + session id, block index) and reads it back through L2,
@@ -126,23 +128,40 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
   if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
   for (uint32_t step = 0; step < A.steps; ++step) {
     /* 1. admission: arrival order, a free slot (stack), committed + newcomer <= cap */
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      A.ctl[9] = 0;                       /* the previous step's free tasks are all done */
-      A.ctl[10] = 0;
-      unsigned long long next = A.ctl[2], committed = A.ctl[3], top = A.ctl[8];
-      while (next < A.n_sessions && A.arrive_step[next] <= step && committed + A.blocks[next] <= A.cap_blocks &&
-             top > 0) {
-        const uint32_t slot = A.free_stack[--top];
-        A.slot_session[slot] = (int)next;
-        A.slot_k[slot] = 0;
-        A.slot_acc[3 * slot] = A.slot_acc[3 * slot + 1] = A.slot_acc[3 * slot + 2] = 0;
-        A.sess_out[5 * next + 3] = step;
-        committed += A.blocks[next];
-        ++next;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+      if (lane == 0) {
+        A.ctl[9] = 0;                     /* the previous step's free tasks are all done */
+        A.ctl[10] = 0;
       }
-      A.ctl[2] = next;
-      A.ctl[3] = committed;
-      A.ctl[8] = top;
+      unsigned long long next = A.ctl[2], committed = A.ctl[3], top = A.ctl[8];
+      for (;;) {
+        const unsigned long long i = next + lane;
+        const bool arrived = i < A.n_sessions && A.arrive_step[i] <= step;
+        unsigned long long cum = arrived ? A.blocks[i] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long y = __shfl_up_sync(0xffffffffu, cum, o);
+          if ((int)lane >= o) cum += y;
+        }
+        const bool ok = arrived && committed + cum <= A.cap_blocks && lane < top;
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        const unsigned n_adm = okm == 0xffffffffu ? 32u : (unsigned)(__ffs(~okm) - 1);   /* leading run */
+        if (lane < n_adm) {
+          const uint32_t slot = A.free_stack[top - 1 - lane];
+          A.slot_session[slot] = (int)i;
+          A.slot_k[slot] = 0;
+          A.slot_acc[3 * slot] = A.slot_acc[3 * slot + 1] = A.slot_acc[3 * slot + 2] = 0;
+          A.sess_out[5 * i + 3] = step;
+        }
+        if (n_adm) committed += __shfl_sync(0xffffffffu, cum, n_adm - 1);
+        next += n_adm;
+        top -= n_adm;
+        if (n_adm < 32) break;
+      }
+      if (lane == 0) {
+        A.ctl[2] = next;
+        A.ctl[3] = committed;
+        A.ctl[8] = top;
+      }
       __threadfence();
     }
     if (!grid_barrier(A.ctl, gridDim.x, A.spin_limit)) return;
