@@ -769,7 +769,7 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
  * batch), then the warp writes the new page ids into the debt slots.  If the
  * heap (or the page-array capacity) is exhausted, the remaining debt slots
  * get the null marker. */
-template <int V>
+template <int V, int FILL = 1>
 __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
   constexpr int QF = ouro_qform(V);
   constexpr bool VL = QF != OURO_QF_RING;
@@ -827,8 +827,8 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
     const unsigned long long total = (unsigned long long)m << ppc_log;
     /* FILL positions per lane per round: their first compare-and-swaps are
      * issued back to back (independent), then checked; a slot that was not
-     * plainly empty falls back to put_at */
-    constexpr int FILL = 1;
+     * plainly empty falls back to put_at.  FILL = 1 keeps the callers'
+     * registers free; latency-bound callers take more in flight. */
     for (unsigned long long i0 = 0; i0 < total; i0 += (unsigned long long)nl * FILL) {
       unsigned long long *cell[FILL];
       unsigned item[FILL];
@@ -977,7 +977,7 @@ __device__ __noinline__ void run_carve(const ouro_heap_dev &h, int c, unsigned v
  * class (any mix of classes); a lane with cls < 0 asks for nothing and only
  * helps: it takes part in the warp's carves, so that a warp in which one
  * lane allocates still fills new slots 32 lanes wide. */
-template <int V>
+template <int V, int FILL = 1>
 __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   constexpr int QF = ouro_qform(V);
   constexpr bool VL = QF != OURO_QF_RING;
@@ -1027,7 +1027,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
           lockers &= lockers - 1;
           const int cj = __shfl_sync(vmask, cls, j);
           if (cj >= (int)h.n_classes) run_carve<V>(h, cj, vmask, j);
-          else page_carve<V>(h, cj, vmask, j);
+          else page_carve<V, FILL>(h, cj, vmask, j);
         }
       }
       const unsigned waiting = __ballot_sync(vmask, st == 0);

@@ -11,14 +11,15 @@ namespace detail {
 
 
 /* Variant-resolved malloc.  want = false: the lane asks for nothing but
- * stays in the call to help its warp carve (see page_malloc). */
-template <int V>
+ * stays in the call to help its warp carve (see page_malloc).  FILL: slot
+ * writes in flight per lane when the warp fills a carve (page queues). */
+template <int V, int FILL = 1>
 __device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long long n, bool want = true) {
   const unsigned mask = __activemask();
   const int cls = want ? size_class(h, n) : -1;
   if (want && cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
   if (!__any_sync(mask, cls >= 0)) return nullptr;
-  if constexpr (ouro_page_queues(V)) return page_malloc<V>(h, cls, mask);   /* pages and runs */
+  if constexpr (ouro_page_queues(V)) return page_malloc<V, FILL>(h, cls, mask);   /* pages and runs */
   else return chunk_or_run_malloc<V>(h, cls, mask);
 }
 

@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(256) k_serve(serve_args A) {
       const uint32_t k = A.slot_k[slot];
       if (k >= A.blocks[sess]) continue;
       /* lane 0 asks; the other 31 lanes help the warp's carves */
-      unsigned long long bp = reinterpret_cast<unsigned long long>(malloc_v<V>(h, A.block_bytes, lane == 0));
+      /* (a step's growth can carve thousands of chunks: eight slot writes per
+       *  lane in flight while the warp fills them) */
+      unsigned long long bp = reinterpret_cast<unsigned long long>(malloc_v<V, 8>(h, A.block_bytes, lane == 0));
       if (lane == 0) {
         if (bp) {
           A.tables[(size_t)slot * A.max_blocks + k] = bp;
