@@ -465,8 +465,26 @@ __device__ inline void va_prefetch(const ouro_heap_dev &h, int c, unsigned s32) 
  * otherwise null while it does not exist.  Null too for a segment that has
  * retired already (only a look-ahead can ask for one: a thread holding an
  * unfinished position keeps its segment alive). */
-__device__ inline unsigned long long *va_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
-                                              bool create) {
+static __device__ __noinline__ unsigned long long *va_slot_wait(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                                               bool create);
+
+__device__ __forceinline__ unsigned long long *va_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                                       bool create) {
+  const unsigned long long s = pos / h.seg_cap;
+  const unsigned s32 = (unsigned)s;
+  const unsigned off = (unsigned)(pos - s * h.seg_cap);
+  const unsigned long long v = ld_acq(va_entry(h, c, s));
+  if (hi32(v) == s32 && lo32(v) < OURO_BUSY) {
+    if (create && off - (h.seg_cap >> 3) < 32u) va_prefetch(h, c, s32 + 1);
+    return seg_cells(h, lo32(v)) + off;
+  }
+  return va_slot_wait(h, c, pos, create);
+}
+
+/* the lookup of a segment that is not in place yet: out of line, it is the
+ * slow path */
+static __device__ __noinline__ unsigned long long *va_slot_wait(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                                               bool create) {
   const unsigned long long s = pos / h.seg_cap;
   const unsigned s32 = (unsigned)s;
   const unsigned off = (unsigned)(pos - s * h.seg_cap);
@@ -561,8 +579,11 @@ __device__ inline void vl_prefetch(const ouro_heap_dev &h, int c, unsigned long 
  * missing segments (producers); otherwise null while the segment is not
  * linked yet.  One thread creates each segment: it first claims the empty
  * link (next = OURO_BUSY); others wait for the link instead of creating. */
-__device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
-                                              bool create) {
+static __device__ __noinline__ unsigned long long *vl_slot_walk(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                                        bool create);
+
+__device__ __forceinline__ unsigned long long *vl_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                                       bool create) {
   ouro_qhdr *q = qh(h, c);
   const unsigned long long s = pos / h.seg_cap;
   const unsigned s32 = (unsigned)s;
@@ -572,6 +593,16 @@ __device__ inline unsigned long long *vl_slot(const ouro_heap_dev &h, int c, uns
     if (create && off - (h.seg_cap >> 3) < 32u) vl_prefetch(h, c, e);
     return seg_cells(h, lo32(e)) + off;
   }
+  return vl_slot_walk(h, c, pos, create);
+}
+
+/* the lookup past a missed hint: out of line, it is the slow path */
+static __device__ __noinline__ unsigned long long *vl_slot_walk(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                                        bool create) {
+  ouro_qhdr *q = qh(h, c);
+  const unsigned long long s = pos / h.seg_cap;
+  const unsigned s32 = (unsigned)s;
+  const unsigned off = (unsigned)(pos - s * h.seg_cap);
   unsigned ns = h.backoff_min_ns;
   unsigned long long cur = 0;
   bool walking = false;

@@ -1,8 +1,11 @@
 """Build the CUDA library libouro.so in-tree for sm_103a (GB300).
 
 Each translation unit is compiled in parallel with nvcc, then linked into one
-shared library next to this file.  No torch extension machinery: the library
-exposes a plain C ABI (include/ouro.h).
+shared library next to this file.  The kernel files are compiled once per
+queue form (-DOURO_SHARD=<form>) plus once for their host entry points
+(-DOURO_SHARD=-1), so the six forms' device code compiles side by side.  No
+torch extension machinery: the library exposes a plain C ABI
+(include/ouro.h).
 """
 from __future__ import annotations
 
@@ -19,7 +22,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libouro.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ouro_host.cu", "ouro_kernels.cu", "ouro_probe.cu", "ouro_batching.cu", "ouro_serving.cu", "ouro_graph.cu"]
+SOURCES = ["ouro_host.cu", "ouro_probe.cu"]
+SHARDED = ["ouro_kernels.cu", "ouro_batching.cu", "ouro_serving.cu", "ouro_graph.cu"]
+N_FORMS = 6                       # ouro_variant values 0..5
+JOBS = [(s, None) for s in SOURCES] + [(s, k) for s in SHARDED for k in range(-1, N_FORMS)]
 
 
 def nvcc() -> str:
@@ -34,13 +40,19 @@ def _flags(extra=()):
             *extra]
 
 
-def _compile(src: str, extra=()) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(job, extra=()) -> str:
+    src, shard = job
+    stem = os.path.splitext(src)[0]
+    if shard is None:
+        obj = os.path.join(BUILD, stem + ".o")
+    else:
+        obj = os.path.join(BUILD, f"{stem}.{'entries' if shard < 0 else f'form{shard}'}.o")
+        extra = (f"-DOURO_SHARD={shard}", *extra)
     cmd = [nvcc(), *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
-    if extra and r.stderr:
+    if "-v" in extra and r.stderr:
         print(r.stderr, file=sys.stderr)     # e.g. -Xptxas -v: registers, spills, shared memory
     return obj
 
@@ -59,8 +71,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and not extra and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
+    # the long jobs (the probes, then the per-form objects) first
+    jobs = sorted(JOBS, key=lambda j: 0 if j[0] == "ouro_probe.cu" else 1 if (j[1] or 0) >= 0 and j[1] is not None else 2)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(lambda j: _compile(j, extra), jobs))
     tmp = f"{LIB}.{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -13,10 +13,12 @@
  * Request i of batch b uses pattern seed (seed + b) and thread id i (its
  * index inside the batch), in every form, so the per-batch checks agree.
  */
+#include <algorithm>
 #include <vector>
 
 #include "ouro_internal.cuh"
 #include "ouro_payload.cuh"
+#include "ouro_shard.cuh"
 
 using namespace ouro::detail;
 
@@ -73,6 +75,52 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+/* ------------------------------------------------------- per-form launchers */
+namespace ouro {
+namespace launch {
+
+template <int V, bool STAGE>
+int persistent_blocks_per_sm(int blocks_per_sm) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<V, STAGE>, 256, 0);
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+  return per_sm;
+}
+
+template <int V>
+ouro_status batches_persistent(ouro_heap *H, const uint32_t *d_sizes, const unsigned long long *d_offs,
+                               const unsigned long long *d_task_offs, uint32_t n_batches, uint64_t n_tasks,
+                               uint32_t seed, int mode, ouro_check *d_out, unsigned long long *d_work,
+                               int blocks_per_sm, cudaStream_t s) {
+  if (H->d.staging) {
+    const int per_sm = std::max(1, persistent_blocks_per_sm<V, true>(blocks_per_sm));
+    k_batches_persistent<V, true><<<per_sm * ouro::host::sm_count(), 256, 0, s>>>(
+        H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
+  } else {
+    const int per_sm = std::max(1, persistent_blocks_per_sm<V, false>(blocks_per_sm));
+    k_batches_persistent<V, false><<<per_sm * ouro::host::sm_count(), 256, 0, s>>>(
+        H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
+  }
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+/* blocks of 256 per SM the unstaged persistent kernel keeps resident */
+template <int V>
+int batches_max_blocks_per_sm() { return persistent_blocks_per_sm<V, false>(0); }
+
+#define INST_BATCHES_PERSISTENT(PRE, V)                                                                         \
+  PRE template ouro_status batches_persistent<V>(ouro_heap *, const uint32_t *, const unsigned long long *,   \
+                                                 const unsigned long long *, uint32_t, uint64_t, uint32_t, int, \
+                                                 ouro_check *, unsigned long long *, int, cudaStream_t);
+#define INST_BATCHES_MAX_BLOCKS(PRE, V) PRE template int batches_max_blocks_per_sm<V>();
+OURO_SHARD_INSTANTIATE(INST_BATCHES_PERSISTENT)
+OURO_SHARD_INSTANTIATE(INST_BATCHES_MAX_BLOCKS)
+
+}  // namespace launch
+}  // namespace ouro
+
+#if OURO_SHARD_ENTRIES
 struct ouro_batch_graph {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
@@ -89,41 +137,20 @@ extern "C" ouro_status ouro_batches_persistent(ouro_heap *H, const uint32_t *d_s
   OURO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(ouro_check) * n_batches, S(stream)));
   OURO_CUDA(cudaMemsetAsync(d_work, 0, 8, S(stream)));
   if (!n_tasks) return OURO_OK;
-  int per_sm = 0;
-  if (H->d.staging) {
-    OURO_DISPATCH(H->d.variant, ({
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<V, true>, 256, 0);
-      if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
-      if (per_sm < 1) per_sm = 1;
-      k_batches_persistent<V, true><<<per_sm * ouro::host::sm_count(), 256, 0, S(stream)>>>(
-          H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
-    }));
-  } else {
-    OURO_DISPATCH(H->d.variant, ({
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<V, false>, 256, 0);
-      if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
-      if (per_sm < 1) per_sm = 1;
-      k_batches_persistent<V, false><<<per_sm * ouro::host::sm_count(), 256, 0, S(stream)>>>(
-          H->d, d_sizes, d_offs, d_task_offs, n_batches, seed, mode, d_out, d_work, n_tasks);
-    }));
-  }
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant,
+                return ouro::launch::batches_persistent<V>(H, d_sizes, d_offs, d_task_offs, n_batches, n_tasks, seed,
+                                                           mode, d_out, d_work, blocks_per_sm, S(stream)));
 }
 
 extern "C" int ouro_batches_max_blocks_per_sm(const ouro_heap *H) {
   if (!H) return 0;
-  int per_sm = 0;
   switch (H->d.variant) {
-    case OURO_PAGE_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_ARRAY, false>, 256, 0); break;
-    case OURO_PAGE_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_VLIST, false>, 256, 0); break;
-    case OURO_CHUNK_ARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_ARRAY, false>, 256, 0); break;
-    case OURO_CHUNK_VLIST: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_VLIST, false>, 256, 0); break;
-    case OURO_PAGE_VARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_PAGE_VARRAY, false>, 256, 0); break;
-    case OURO_CHUNK_VARRAY: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batches_persistent<OURO_CHUNK_VARRAY, false>, 256, 0); break;
-    default: break;
+#define CASE_MAX_BLOCKS(PRE, V) \
+  case V: return ouro::launch::batches_max_blocks_per_sm<V>();
+    OURO_SHARD_EACH(CASE_MAX_BLOCKS, )
+#undef CASE_MAX_BLOCKS
+    default: return 0;
   }
-  return per_sm;
 }
 
 /* Capture the per-batch launches of one pass over all batches.
@@ -201,3 +228,4 @@ extern "C" ouro_status ouro_batch_graph_destroy(ouro_batch_graph *G) {
   delete G;
   return OURO_OK;
 }
+#endif

@@ -18,6 +18,7 @@
  */
 #include "ouro_internal.cuh"
 #include "ouro_payload.cuh"
+#include "ouro_shard.cuh"
 
 using namespace ouro::detail;
 
@@ -266,27 +267,63 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+/* ------------------------------------------------------- per-form launchers */
+namespace ouro {
+namespace launch {
+
+template <int V>
+ouro_status graph_init(ouro_heap *H, void *d_vertices, uint32_t n_vertices, unsigned long long *d_ctl,
+                       cudaStream_t s) {
+  k_graph_init<V><<<4 * ouro::host::sm_count(), 256, 0, s>>>(H->d, (vertex *)d_vertices, n_vertices, d_ctl);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+template <int V>
+ouro_status graph_insert(ouro_heap *H, void *d_vertices, const uint32_t *d_src, const uint32_t *d_dst,
+                         uint64_t n_edges, unsigned long long *d_ctl, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((n_edges + GB_EDGES - 1) / GB_EDGES);
+  k_graph_insert<V><<<blocks, GB_THREADS, 0, s>>>(H->d, (vertex *)d_vertices, d_src, d_dst, n_edges, d_ctl);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+template <int V>
+ouro_status graph_free(ouro_heap *H, void *d_vertices, uint32_t n_vertices, cudaStream_t s) {
+  k_graph_free<V><<<4 * ouro::host::sm_count(), 256, 0, s>>>(H->d, (vertex *)d_vertices, n_vertices);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+#define INST_GRAPH_INIT(PRE, V) \
+  PRE template ouro_status graph_init<V>(ouro_heap *, void *, uint32_t, unsigned long long *, cudaStream_t);
+#define INST_GRAPH_INSERT(PRE, V)                                                                          \
+  PRE template ouro_status graph_insert<V>(ouro_heap *, void *, const uint32_t *, const uint32_t *, uint64_t, \
+                                           unsigned long long *, cudaStream_t);
+#define INST_GRAPH_FREE(PRE, V) PRE template ouro_status graph_free<V>(ouro_heap *, void *, uint32_t, cudaStream_t);
+OURO_SHARD_INSTANTIATE(INST_GRAPH_INIT)
+OURO_SHARD_INSTANTIATE(INST_GRAPH_INSERT)
+OURO_SHARD_INSTANTIATE(INST_GRAPH_FREE)
+
+}  // namespace launch
+}  // namespace ouro
+
+#if OURO_SHARD_ENTRIES
 extern "C" size_t ouro_graph_vertex_bytes(void) { return sizeof(vertex); }
 
 extern "C" ouro_status ouro_graph_init(ouro_heap *H, void *d_vertices, uint32_t n_vertices, unsigned long long *d_ctl,
                                        void *stream) {
   if (!H || !d_vertices || !d_ctl || !n_vertices) return OURO_EINVAL;
   OURO_CUDA(cudaMemsetAsync(d_ctl, 0, 4 * 8, S(stream)));
-  const int g = 4 * ouro::host::sm_count();
-  OURO_DISPATCH(H->d.variant, (k_graph_init<V><<<g, 256, 0, S(stream)>>>(H->d, (vertex *)d_vertices, n_vertices, d_ctl)));
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant, return ouro::launch::graph_init<V>(H, d_vertices, n_vertices, d_ctl, S(stream)));
 }
 
 extern "C" ouro_status ouro_graph_insert(ouro_heap *H, void *d_vertices, const uint32_t *d_src, const uint32_t *d_dst,
                                          uint64_t n_edges, unsigned long long *d_ctl, void *stream) {
   if (!H || !d_vertices || !d_ctl || (n_edges && (!d_src || !d_dst))) return OURO_EINVAL;
   if (!n_edges) return OURO_OK;
-  const unsigned blocks = (unsigned)((n_edges + GB_EDGES - 1) / GB_EDGES);
-  OURO_DISPATCH(H->d.variant, (k_graph_insert<V><<<blocks, GB_THREADS, 0, S(stream)>>>(
-                                   H->d, (vertex *)d_vertices, d_src, d_dst, n_edges, d_ctl)));
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant,
+                return ouro::launch::graph_insert<V>(H, d_vertices, d_src, d_dst, n_edges, d_ctl, S(stream)));
 }
 
 extern "C" ouro_status ouro_graph_gather(ouro_heap *H, const void *d_vertices, uint32_t n_vertices,
@@ -300,8 +337,6 @@ extern "C" ouro_status ouro_graph_gather(ouro_heap *H, const void *d_vertices, u
 
 extern "C" ouro_status ouro_graph_free(ouro_heap *H, void *d_vertices, uint32_t n_vertices, void *stream) {
   if (!H || !d_vertices) return OURO_EINVAL;
-  const int g = 4 * ouro::host::sm_count();
-  OURO_DISPATCH(H->d.variant, (k_graph_free<V><<<g, 256, 0, S(stream)>>>(H->d, (vertex *)d_vertices, n_vertices)));
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant, return ouro::launch::graph_free<V>(H, d_vertices, n_vertices, S(stream)));
 }
+#endif

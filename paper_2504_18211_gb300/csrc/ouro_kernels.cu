@@ -13,6 +13,7 @@
  */
 #include "ouro_internal.cuh"
 #include "ouro_payload.cuh"
+#include "ouro_shard.cuh"
 
 using namespace ouro::detail;
 
@@ -110,26 +111,67 @@ inline int grid_for(size_t n, int block, int cap) {
 
 }  // namespace
 
+/* ------------------------------------------------------- per-form launchers */
+namespace ouro {
+namespace launch {
+
+template <int V>
+ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n, cudaStream_t s) {
+  const int block = 256;
+  k_batch_malloc<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+template <int V>
+ouro_status batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, cudaStream_t s) {
+  const int block = 256;
+  k_batch_free<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+template <int V>
+ouro_status round_fused(ouro_heap *H, const uint32_t *d_sizes, size_t n, uint32_t seed, int mode, ouro_check *d_out,
+                        void **d_ptrs, unsigned long long *work, cudaStream_t s) {
+  const int block = 256;
+  if (H->d.staging)
+    k_round_fused<V, true><<<grid_for(n, block, occupancy_grid(k_round_fused<V, true>, block)), block, 0, s>>>(
+        H->d, d_sizes, n, seed, mode, d_out, d_ptrs, work);
+  else
+    k_round_fused<V, false><<<grid_for(n, block, occupancy_grid(k_round_fused<V, false>, block)), block, 0, s>>>(
+        H->d, d_sizes, n, seed, mode, d_out, d_ptrs, work);
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+#define INST_BATCH_MALLOC(PRE, V) \
+  PRE template ouro_status batch_malloc<V>(ouro_heap *, const uint32_t *, void **, size_t, cudaStream_t);
+#define INST_BATCH_FREE(PRE, V) \
+  PRE template ouro_status batch_free<V>(ouro_heap *, void *const *, size_t, cudaStream_t);
+#define INST_ROUND_FUSED(PRE, V)                                                                                 \
+  PRE template ouro_status round_fused<V>(ouro_heap *, const uint32_t *, size_t, uint32_t, int, ouro_check *, \
+                                          void **, unsigned long long *, cudaStream_t);
+OURO_SHARD_INSTANTIATE(INST_BATCH_MALLOC)
+OURO_SHARD_INSTANTIATE(INST_BATCH_FREE)
+OURO_SHARD_INSTANTIATE(INST_ROUND_FUSED)
+
+}  // namespace launch
+}  // namespace ouro
+
+#if OURO_SHARD_ENTRIES
 /* ------------------------------------------------------------- C entries */
 extern "C" ouro_status ouro_batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n,
                                          void *stream) {
   if (!H || (n && (!d_sizes || !d_ptrs))) return OURO_EINVAL;
   if (!n) return OURO_OK;
-  const int block = 256;
-  const int g = grid_for(n, block, 1 << 20);
-  OURO_DISPATCH(H->d.variant, (k_batch_malloc<V><<<g, block, 0, S(stream)>>>(H->d, d_sizes, d_ptrs, n)));
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant, return ouro::launch::batch_malloc<V>(H, d_sizes, d_ptrs, n, S(stream)));
 }
 
 extern "C" ouro_status ouro_batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, void *stream) {
   if (!H || (n && !d_ptrs)) return OURO_EINVAL;
   if (!n) return OURO_OK;
-  const int block = 256;
-  const int g = grid_for(n, block, 1 << 20);
-  OURO_DISPATCH(H->d.variant, (k_batch_free<V><<<g, block, 0, S(stream)>>>(H->d, d_ptrs, n)));
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant, return ouro::launch::batch_free<V>(H, d_ptrs, n, S(stream)));
 }
 
 extern "C" ouro_status ouro_pattern_write(void *const *d_ptrs, const uint32_t *d_sizes, size_t n, uint32_t seed,
@@ -168,16 +210,7 @@ extern "C" ouro_status ouro_round_fused(ouro_heap *H, const uint32_t *d_sizes, s
   const unsigned slot = __atomic_fetch_add(&H->work_seq, 1u, __ATOMIC_RELAXED) % OURO_WORK_SLOTS;
   unsigned long long *work = (unsigned long long *)(H->meta + H->off_work + (size_t)slot * 128);
   OURO_CUDA(cudaMemsetAsync(work, 0, 8, S(stream)));
-  const int block = 256;
-  if (H->d.staging) {
-    OURO_DISPATCH(H->d.variant, (k_round_fused<V, true><<<grid_for(n, block, occupancy_grid(k_round_fused<V, true>, block)),
-                                                         block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs,
-                                                                                work)));
-  } else {
-    OURO_DISPATCH(H->d.variant, (k_round_fused<V, false><<<grid_for(n, block, occupancy_grid(k_round_fused<V, false>, block)),
-                                                          block, 0, S(stream)>>>(H->d, d_sizes, n, seed, mode, d_out, d_ptrs,
-                                                                                 work)));
-  }
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant,
+                return ouro::launch::round_fused<V>(H, d_sizes, n, seed, mode, d_out, d_ptrs, work, S(stream)));
 }
+#endif

@@ -26,6 +26,7 @@
  */
 #include "ouro_internal.cuh"
 #include "ouro_payload.cuh"
+#include "ouro_shard.cuh"
 
 using namespace ouro::detail;
 
@@ -266,6 +267,31 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+/* ------------------------------------------------------- per-form launcher */
+namespace ouro {
+namespace launch {
+
+/* args: the kernel's serve_args, set up by ouro_serve */
+template <int V>
+ouro_status serve(const void *args, int blocks_per_sm, cudaStream_t s) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<V>, 256, 0);
+  if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+  if (per_sm < 1) per_sm = 1;
+  void *argv[] = {const_cast<void *>(args)};
+  OURO_CUDA(cudaLaunchCooperativeKernel((const void *)k_serve<V>, dim3(per_sm * ouro::host::sm_count()), dim3(256),
+                                        argv, 0, s));
+  OURO_LAUNCHED();
+  return OURO_OK;
+}
+
+#define INST_SERVE(PRE, V) PRE template ouro_status serve<V>(const void *, int, cudaStream_t);
+OURO_SHARD_INSTANTIATE(INST_SERVE)
+
+}  // namespace launch
+}  // namespace ouro
+
+#if OURO_SHARD_ENTRIES
 extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, const uint32_t *d_blocks,
                                   uint32_t n_sessions, uint32_t n_slots, uint32_t max_blocks, int *d_slot_session,
                                   uint32_t *d_slot_k, unsigned long long *d_slot_acc, unsigned long long *d_tables,
@@ -301,18 +327,10 @@ extern "C" ouro_status ouro_serve(ouro_heap *H, const uint32_t *d_arrive_step, c
   A.cap_blocks = cap_blocks;
   A.block_bytes = block_bytes;
   A.spin_limit = 1u << 24;   /* barrier wait: ~2 s of 128 ns naps, far above any step */
-  int dev = 0, coop = 0, per_sm = 0;
+  int dev = 0, coop = 0;
   OURO_CUDA(cudaGetDevice(&dev));
   OURO_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return OURO_ENOTSUP;
-  void *args[] = {&A};
-  OURO_DISPATCH(H->d.variant, ({
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve<V>, 256, 0);
-    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
-    if (per_sm < 1) per_sm = 1;
-    OURO_CUDA(cudaLaunchCooperativeKernel((const void *)k_serve<V>, dim3(per_sm * ouro::host::sm_count()),
-                                          dim3(256), args, 0, s));
-  }));
-  OURO_LAUNCHED();
-  return OURO_OK;
+  OURO_DISPATCH(H->d.variant, return ouro::launch::serve<V>(&A, blocks_per_sm, s));
 }
+#endif
