@@ -302,10 +302,10 @@ ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
  *   d_step_ns 3*`steps` %globaltimer stamps (after admission, growth and
  *   completion of each step), d_ctl 11 words (barrier state, next
  *   arrival, committed blocks, error flag, mallocs, frees, failed mallocs,
- *   free-slot stack top, sessions finished and free tasks taken in the
- *   step), d_free_stack 2*n_slots slot ids (the free-slot stack, then the
- *   step's list of finished sessions, whose blocks every warp helps free
- *   in tasks of 256).
+ *   free-slot stack top, sessions finished in the step, one reserved),
+ *   d_free_stack 2*n_slots slot ids (the free-slot stack, then the step's
+ *   list of finished sessions, whose blocks are freed in tasks of 32 dealt
+ *   to the warps in turn).
  * ENOTSUP if the device cannot launch cooperative kernels.  A grid barrier
  * whose wait runs out sets d_ctl[4] and ends the kernel. */
 ouro_status ouro_serve(ouro_heap *h, const uint32_t *d_arrive_step, const uint32_t *d_blocks, uint32_t n_sessions,
@@ -314,6 +314,21 @@ ouro_status ouro_serve(ouro_heap *h, const uint32_t *d_arrive_step, const uint32
                        unsigned long long *d_step_ns, unsigned long long *d_ctl, uint32_t *d_free_stack,
                        uint32_t steps, uint32_t seed, uint64_t cap_blocks, uint32_t block_bytes, int blocks_per_sm,
                        void *stream);
+
+/* The same loop as plain per-launch kernels: for every step, one launch each
+ * for admission, growth, completion and freeing, enqueued on `stream` in
+ * order without a host wait (4 * steps + 2 launches).  Kernel boundaries
+ * take the place of the grid barriers, so no cooperative launch is needed
+ * and no wait can run out.  Arguments, buffers and results are those of
+ * ouro_serve and equal its results for the same inputs; d_step_ns stamps
+ * are taken at the start of the next phase's launch.  An added comparison
+ * form: the paper's driver launches one kernel per phase (Sec. 3). */
+ouro_status ouro_serve_per_launch(ouro_heap *h, const uint32_t *d_arrive_step, const uint32_t *d_blocks,
+                                  uint32_t n_sessions, uint32_t n_slots, uint32_t max_blocks, int *d_slot_session,
+                                  uint32_t *d_slot_k, unsigned long long *d_slot_acc, unsigned long long *d_tables,
+                                  unsigned long long *d_sess_out, unsigned long long *d_step_ns,
+                                  unsigned long long *d_ctl, uint32_t *d_free_stack, uint32_t steps, uint32_t seed,
+                                  uint64_t cap_blocks, uint32_t block_bytes, int blocks_per_sm, void *stream);
 
 /* ---- graph growth: adjacency lists grown in kernels --------------------------- */
 

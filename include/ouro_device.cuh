@@ -173,10 +173,14 @@ __host__ __device__ __forceinline__ ouro_qhdr *qh(const ouro_heap_dev &h, int c)
 __device__ __forceinline__ ouro_glob *gl(const ouro_heap_dev &h) {
   return reinterpret_cast<ouro_glob *>(h.glob);
 }
+/* statistics counter, sharded by SM; a reduction (no value returned), so the
+ * thread never waits for it */
 __device__ __forceinline__ void stat_add(const ouro_heap_dev &h, int row, int kind,
                                          unsigned long long v) {
-  if (v)
-    atomicAdd(&h.stats[((size_t)row * OURO_NSTAT + kind) * OURO_SHARDS + (smid() & (OURO_SHARDS - 1))], v);
+  if (v) {
+    unsigned long long *a = &h.stats[((size_t)row * OURO_NSTAT + kind) * OURO_SHARDS + (smid() & (OURO_SHARDS - 1))];
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+  }
 }
 /* error sites: where the first recorded error of a heap came from */
 enum {
@@ -465,26 +469,8 @@ __device__ inline void va_prefetch(const ouro_heap_dev &h, int c, unsigned s32) 
  * otherwise null while it does not exist.  Null too for a segment that has
  * retired already (only a look-ahead can ask for one: a thread holding an
  * unfinished position keeps its segment alive). */
-static __device__ __noinline__ unsigned long long *va_slot_wait(const ouro_heap_dev &h, int c, unsigned long long pos,
-                                                               bool create);
-
-__device__ __forceinline__ unsigned long long *va_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
-                                                       bool create) {
-  const unsigned long long s = pos / h.seg_cap;
-  const unsigned s32 = (unsigned)s;
-  const unsigned off = (unsigned)(pos - s * h.seg_cap);
-  const unsigned long long v = ld_acq(va_entry(h, c, s));
-  if (hi32(v) == s32 && lo32(v) < OURO_BUSY) {
-    if (create && off - (h.seg_cap >> 3) < 32u) va_prefetch(h, c, s32 + 1);
-    return seg_cells(h, lo32(v)) + off;
-  }
-  return va_slot_wait(h, c, pos, create);
-}
-
-/* the lookup of a segment that is not in place yet: out of line, it is the
- * slow path */
-static __device__ __noinline__ unsigned long long *va_slot_wait(const ouro_heap_dev &h, int c, unsigned long long pos,
-                                                               bool create) {
+__device__ inline unsigned long long *va_slot(const ouro_heap_dev &h, int c, unsigned long long pos,
+                                              bool create) {
   const unsigned long long s = pos / h.seg_cap;
   const unsigned s32 = (unsigned)s;
   const unsigned off = (unsigned)(pos - s * h.seg_cap);
@@ -1008,8 +994,8 @@ __device__ __noinline__ void run_carve(const ouro_heap_dev &h, int c, unsigned v
  * class (any mix of classes); a lane with cls < 0 asks for nothing and only
  * helps: it takes part in the warp's carves, so that a warp in which one
  * lane allocates still fills new slots 32 lanes wide. */
-template <int V, int FILL = 1>
-__device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
+template <int V, int FILL = 1, bool RESERVED = false>
+__device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, unsigned long long p0_reserved = 0) {
   constexpr int QF = ouro_qform(V);
   constexpr bool VL = QF != OURO_QF_RING;
   const bool req = cls >= 0;
@@ -1019,8 +1005,9 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   const unsigned leader = __ffs(grp) - 1;
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long pos = 0;
-  if (req && lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
-  const unsigned long long p0 = __shfl_sync(vmask, pos, leader);
+  if (RESERVED) pos = p0_reserved;   /* the caller took the group's head positions (block aggregation) */
+  else if (req && lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
+  const unsigned long long p0 = RESERVED ? pos : __shfl_sync(vmask, pos, leader);
   pos = p0 + rank;
 
   unsigned item = 0;
@@ -1102,18 +1089,22 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
       res = h.base + ((size_t)item << (4 + cls));
     }
   }
-  /* per-class counters, one update per class group of the warp */
-  const unsigned g2 = warp_group(h, vmask, cls);
-  const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
-  if (req && lane == (unsigned)(__ffs(g2) - 1)) {
-    stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
-    stat_add(h, cls, OURO_ST_FAILED, __popc(g2) - __popc(okm));
+  /* per-class counters, one update per class group of the warp (a caller
+   * with reserved positions counts for its whole block) */
+  if (!RESERVED) {
+    const unsigned g2 = warp_group(h, vmask, cls);
+    const unsigned okm = __ballot_sync(vmask, st == 1) & g2;
+    if (req && lane == (unsigned)(__ffs(g2) - 1)) {
+      stat_add(h, cls, OURO_ST_MALLOC, __popc(okm));
+      stat_add(h, cls, OURO_ST_FAILED, __popc(g2) - __popc(okm));
+    }
   }
   return res;
 }
 
-template <int V>
-__device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsigned vmask) {
+template <int V, bool RESERVED = false>
+__device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsigned vmask,
+                          unsigned long long t0_reserved = 0) {
   constexpr int QF = ouro_qform(V);
   constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, cls);
@@ -1122,11 +1113,13 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
   const unsigned leader = __ffs(grp) - 1;
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long t = 0;
-  if (lane == leader) {
+  if (RESERVED) {
+    t = t0_reserved;   /* the caller took the group's tail positions and counted the frees */
+  } else if (lane == leader) {
     t = atomicAdd(&q->tail.v, (unsigned long long)__popc(grp));
     stat_add(h, cls, OURO_ST_FREE, __popc(grp));
   }
-  const unsigned long long t0 = __shfl_sync(vmask, t, leader);
+  const unsigned long long t0 = RESERVED ? t : __shfl_sync(vmask, t, leader);
   t = t0 + rank;
   unsigned long long *cell;
   if (VL) {   /* the leader finds (or links) its segment; lanes in the same segment reuse it */

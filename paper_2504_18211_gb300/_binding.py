@@ -113,6 +113,8 @@ def load(path: str = LIB_PATH):
         "ouro_batch_graph_destroy": (st, [vp]),
         "ouro_batches_max_blocks_per_sm": (i32, [vp]),
         "ouro_serve": (st, [vp, vp, vp, u32, u32, u32, vp, vp, vp, vp, vp, vp, vp, vp, u32, u32, u64, u32, i32, vp]),
+        "ouro_serve_per_launch": (st, [vp, vp, vp, u32, u32, u32, vp, vp, vp, vp, vp, vp, vp, vp, u32, u32, u64, u32,
+                                       i32, vp]),
         "ouro_graph_vertex_bytes": (sz, []),
         "ouro_graph_init": (st, [vp, vp, u32, vp, vp]),
         "ouro_graph_insert": (st, [vp, vp, vp, vp, u64, vp, vp]),

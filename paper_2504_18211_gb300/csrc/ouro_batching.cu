@@ -71,7 +71,9 @@ k_batches_persistent(ouro_heap_dev h, const uint32_t *sizes, const unsigned long
   if (STAGE) ouro_block_end_v<V>(ctx, h);
 }
 
+#if OURO_SHARD_ENTRIES
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+#endif
 
 }  // namespace
 

@@ -263,7 +263,9 @@ __global__ void k_graph_free(ouro_heap_dev h, vertex *vt, unsigned nv) {
   }
 }
 
+#if OURO_SHARD_ENTRIES
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+#endif
 
 }  // namespace
 

@@ -31,6 +31,77 @@ __global__ void k_batch_free(ouro_heap_dev h, void *const *ptrs, size_t n) {
     free_v<V>(h, ptrs[i]);
 }
 
+/* Block-aggregated forms (page queues, not the deoptimised form): the warps
+ * of a block count their requests per class in shared memory, and one
+ * thread per class takes the whole block's head (malloc) or tail (free)
+ * positions with a single atomic, so the hot queue counters see one atomic
+ * per class per block instead of one per class per warp.  Each warp then
+ * serves its lanes from the reserved positions as the warp form does, and
+ * the statistics are counted once per class per block. */
+template <int V>
+__global__ void __launch_bounds__(256) k_batch_malloc_blk(ouro_heap_dev h, const uint32_t *sizes, void **ptrs,
+                                                          size_t n) {
+  __shared__ unsigned long long s_cnt[OURO_MAX_CLASSES], s_pos[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
+  const unsigned lane = threadIdx.x & 31;
+  for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = base + threadIdx.x;
+    const bool act = i < n;
+    const uint32_t sz = act ? sizes[i] : 0;
+    const int cls = act ? size_class(h, sz) : -1;
+    if (act && cls < 0) stat_add(h, OURO_ROW_NONE, sz == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+    if (threadIdx.x < OURO_MAX_CLASSES) s_cnt[threadIdx.x] = s_ok[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned grp = __match_any_sync(0xffffffffu, cls);
+    const unsigned leader = __ffs(grp) - 1;
+    unsigned long long off = 0;
+    if (cls >= 0 && lane == leader) off = atomicAdd(&s_cnt[cls], (unsigned long long)__popc(grp));
+    __syncthreads();
+    if (threadIdx.x < OURO_MAX_CLASSES && s_cnt[threadIdx.x])
+      s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->head.v, s_cnt[threadIdx.x]);
+    __syncthreads();
+    const unsigned long long p0 = __shfl_sync(0xffffffffu, cls >= 0 ? s_pos[cls] + off : 0ull, leader);
+    void *p = nullptr;
+    if (__any_sync(0xffffffffu, cls >= 0)) p = page_malloc<V, 1, true>(h, cls, 0xffffffffu, p0);
+    if (act) ptrs[i] = p;
+    const unsigned okm = __ballot_sync(0xffffffffu, p != nullptr) & grp;
+    if (cls >= 0 && lane == leader && okm) atomicAdd(&s_ok[cls], (unsigned long long)__popc(okm));
+    __syncthreads();
+    if (threadIdx.x < OURO_MAX_CLASSES && s_cnt[threadIdx.x]) {
+      stat_add(h, threadIdx.x, OURO_ST_MALLOC, s_ok[threadIdx.x]);
+      stat_add(h, threadIdx.x, OURO_ST_FAILED, s_cnt[threadIdx.x] - s_ok[threadIdx.x]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *const *ptrs, size_t n) {
+  __shared__ unsigned long long s_cnt[OURO_MAX_CLASSES], s_pos[OURO_MAX_CLASSES];
+  const unsigned lane = threadIdx.x & 31;
+  for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = base + threadIdx.x;
+    void *p = i < n ? ptrs[i] : nullptr;
+    unsigned item = 0;
+    const int cls = free_locate<V>(h, p, item);
+    if (threadIdx.x < OURO_MAX_CLASSES) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned grp = __match_any_sync(0xffffffffu, cls);
+    const unsigned leader = __ffs(grp) - 1;
+    unsigned long long off = 0;
+    if (cls >= 0 && lane == leader) off = atomicAdd(&s_cnt[cls], (unsigned long long)__popc(grp));
+    __syncthreads();
+    if (threadIdx.x < OURO_MAX_CLASSES && s_cnt[threadIdx.x]) {
+      s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->tail.v, s_cnt[threadIdx.x]);
+      stat_add(h, threadIdx.x, OURO_ST_FREE, s_cnt[threadIdx.x]);
+    }
+    __syncthreads();
+    const unsigned long long t0 = __shfl_sync(0xffffffffu, cls >= 0 ? s_pos[cls] + off : 0ull, leader);
+    const unsigned vmask = __ballot_sync(0xffffffffu, cls >= 0);
+    if (cls >= 0) page_free<V, true>(h, cls, item, vmask, t0);
+    __syncthreads();
+  }
+}
+
 template <int OP>
 __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, uint32_t seed, int mode,
                           ouro_check *out) {
@@ -93,7 +164,9 @@ __global__ void __launch_bounds__(256, OURO_FUSED_MIN_BLOCKS) k_round_fused(ouro
   flush_acc(a, nulls, out);
 }
 
+#if OURO_SHARD_ENTRIES
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+#endif
 
 template <typename K>
 int occupancy_grid(K kernel, int block) {
@@ -117,16 +190,18 @@ namespace launch {
 
 template <int V>
 ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n, cudaStream_t s) {
-  const int block = 256;
-  k_batch_malloc<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+  const int block = 256, g = grid_for(n, block, 1 << 20);
+  if (ouro_page_queues(V) && !H->d.deopt) k_batch_malloc_blk<V><<<g, block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+  else k_batch_malloc<V><<<g, block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
   OURO_LAUNCHED();
   return OURO_OK;
 }
 
 template <int V>
 ouro_status batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, cudaStream_t s) {
-  const int block = 256;
-  k_batch_free<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
+  const int block = 256, g = grid_for(n, block, 1 << 20);
+  if (ouro_page_queues(V) && !H->d.deopt) k_batch_free_blk<V><<<g, block, 0, s>>>(H->d, d_ptrs, n);
+  else k_batch_free<V><<<g, block, 0, s>>>(H->d, d_ptrs, n);
   OURO_LAUNCHED();
   return OURO_OK;
 }

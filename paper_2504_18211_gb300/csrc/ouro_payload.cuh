@@ -23,10 +23,11 @@ __device__ __forceinline__ void *malloc_v(const ouro_heap_dev &h, unsigned long 
   else return chunk_or_run_malloc<V>(h, cls, mask);
 }
 
+/* Class and item of a block being freed; -1 for null or an invalid free
+ * (recorded).  A run is marked free here; page queues in checked mode clear
+ * the page's bit and catch a double free. */
 template <int V>
-__device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
-  const unsigned mask = __activemask();
-  unsigned item = 0;
+__device__ __forceinline__ int free_locate(const ouro_heap_dev &h, void *p, unsigned &item) {
   int cls = -1;
   if (p) {
     cls = locate(h, p, &item);
@@ -44,6 +45,14 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
       }
     }
   }
+  return cls;
+}
+
+template <int V>
+__device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
+  const unsigned mask = __activemask();
+  unsigned item = 0;
+  const int cls = free_locate<V>(h, p, item);
   if constexpr (!ouro_page_queues(V)) {
     chunk_or_run_free<V>(h, cls, item, p, mask);
   } else {

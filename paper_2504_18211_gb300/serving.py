@@ -34,19 +34,24 @@ class ServeRun:
         self.ctl = torch.zeros(11, dtype=torch.int64, device=dev)
         self.free_stack = torch.empty(2 * n_slots, dtype=torch.int32, device=dev)   # stack, then done list
 
-    def run(self, heap, cap_blocks: int, blocks_per_sm: int = 0) -> float:
-        """One call of the device loop; returns its duration in ms (CUDA events)."""
+    def run(self, heap, cap_blocks: int, blocks_per_sm: int = 0, form: str = "persistent") -> float:
+        """One call of the loop; returns its duration in ms (CUDA events).
+        form "persistent": ouro_serve, every step in one cooperative kernel;
+        "per_launch": ouro_serve_per_launch, four launches per step."""
         torch = self.torch
+        if form not in ("persistent", "per_launch"):
+            raise ValueError(f"unknown serving form {form!r}")
+        fn = B.load().ouro_serve if form == "persistent" else B.load().ouro_serve_per_launch
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s = torch.cuda.current_stream()
         a.record(s)
-        st = B.load().ouro_serve(
+        st = fn(
             C.c_void_p(heap.h), B._ptr(self.d_arrive), B._ptr(self.d_blocks), self.n, self.n_slots,
             self.max_blocks, B._ptr(self.slot_session), B._ptr(self.slot_k), B._ptr(self.slot_acc),
             B._ptr(self.tables), B._ptr(self.sess_out), B._ptr(self.step_ns), B._ptr(self.ctl),
             B._ptr(self.free_stack), self.steps,
             self.seed, cap_blocks, self.block_bytes, blocks_per_sm, B._stream(None))
-        B._check("ouro_serve", st)
+        B._check("ouro_serve" if form == "persistent" else "ouro_serve_per_launch", st)
         b.record(s)
         torch.cuda.synchronize()
         return a.elapsed_time(b)

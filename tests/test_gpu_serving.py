@@ -64,3 +64,41 @@ def test_serving_loop_matches_model_and_oracle(P, variant):
             solo.run(heap2, cap)
             r2 = solo.results()
         assert (int(r2["xor"][0]), int(r2["sum"][0])) == (int(r["xor"][s]), int(r["sum"][s]))
+
+
+@pytest.mark.parametrize("variant", ["page_array", "chunk_array"])
+def test_serving_per_launch_form_equals_loop(P, variant):
+    """The per-launch form (four launches per step) gives the loop's results:
+    the same admission schedule (the host model's), the same per-session
+    checksums and mismatch counts, the same allocator counts."""
+    from paper_2504_18211_gb300.serving import ServeRun, model_schedule
+    torch_cuda()
+    steps, block = 200, 16384
+    arrive, blocks = W.serving_workload(steps=steps, rate=2000.0, dt=0.01, median_bytes=256 << 10, sigma=1.0,
+                                        block_bytes=block, max_blocks=256, seed=W.SEED_BASE + 43)
+    heap_bytes = 128 << 20
+    cap = int(0.95 * heap_bytes // block)
+    got = {}
+    for form in ("persistent", "per_launch"):
+        run = ServeRun(arrive, blocks, n_slots=512, max_blocks=256, steps=steps, seed=0x5E57, block_bytes=block)
+        with P.Heap(heap_bytes, block, variant) as heap:
+            run.run(heap, cap, form=form)
+            r = run.results()
+            st = heap.stats()
+        assert r["error"] == 0 and r["failed"] == 0 and st["error_bits"] == 0, form
+        assert sum(st["live"]) == r["mallocs"] - r["frees"], form
+        assert np.all(np.diff(run.step_ns.cpu().numpy().reshape(-1, 3)[:, 2]) >= 0), form   # stamps in order
+        got[form] = r
+    admit, done, k = model_schedule(arrive, blocks, steps, 512, cap)
+    a, b = got["persistent"], got["per_launch"]
+    assert (done >= 0).sum() > 30 and (admit < 0).sum() > 0
+    for r in (a, b):
+        assert np.array_equal(r["admit"], admit) and np.array_equal(r["done"], done)
+        assert r["mallocs"] == int(k.sum())
+    for key in ("xor", "sum", "mism"):
+        assert np.array_equal(a[key], b[key]), key
+    assert (a["mallocs"], a["frees"]) == (b["mallocs"], b["frees"])
+    fin = np.flatnonzero(done >= 0)
+    assert np.all(b["mism"][fin] == 0)
+    for s in fin[:: max(1, fin.size // 20)]:
+        assert (int(b["xor"][s]), int(b["sum"][s])) == session_checksum(0x5E57, int(s), int(blocks[s]), block), s
