@@ -158,6 +158,15 @@ __device__ __forceinline__ unsigned long long exch_rel(unsigned long long *p, un
   asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(o) : "l"(p), "l"(v) : "memory");
   return o;
 }
+__device__ __forceinline__ unsigned long long cas_rlx(unsigned long long *p, unsigned long long c,
+                                                      unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.relaxed.gpu.global.cas.b64 %0, [%1], %2, %3;"
+               : "=l"(o) : "l"(p), "l"(c), "l"(v) : "memory");
+  return o;
+}
+/* with a relaxed load before it, an acquire; with a relaxed write after it, a release */
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ unsigned long long cas_ar(unsigned long long *p, unsigned long long c,
                                                      unsigned long long v) {
   unsigned long long o;
@@ -995,7 +1004,7 @@ __device__ __noinline__ void run_carve(const ouro_heap_dev &h, int c, unsigned v
  * helps: it takes part in the warp's carves, so that a warp in which one
  * lane allocates still fills new slots 32 lanes wide. */
 template <int V, int FILL = 1, bool RESERVED = false>
-__device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, unsigned long long p0_reserved = 0) {
+__device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, unsigned long long p_reserved = 0) {
   constexpr int QF = ouro_qform(V);
   constexpr bool VL = QF != OURO_QF_RING;
   const bool req = cls >= 0;
@@ -1005,10 +1014,10 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, un
   const unsigned leader = __ffs(grp) - 1;
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long pos = 0;
-  if (RESERVED) pos = p0_reserved;   /* the caller took the group's head positions (block aggregation) */
+  if (RESERVED) pos = p_reserved;    /* the caller took this lane's head position (block aggregation) */
   else if (req && lane == leader) pos = atomicAdd(&q->head.v, (unsigned long long)__popc(grp));
-  const unsigned long long p0 = RESERVED ? pos : __shfl_sync(vmask, pos, leader);
-  pos = p0 + rank;
+  const unsigned long long p0 = __shfl_sync(vmask, pos, leader);   /* the group leader's position */
+  if (!RESERVED) pos = p0 + rank;
 
   unsigned item = 0;
   int st = req ? 0 : 3;   /* 0 waiting, 1 item, 2 null answer, 3 gave up (helpers: nothing asked) */
@@ -1017,7 +1026,8 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, un
     unsigned long long *c0 = (req && lane == leader) ? slot_at<QF>(h, cls, p0, false) : nullptr;
     c0 = reinterpret_cast<unsigned long long *>(
         __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
-    if (req) cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + rank : slot_at<QF>(h, cls, pos, false);
+    if (req)
+      cell = (c0 && pos / h.seg_cap == p0 / h.seg_cap) ? c0 + (long long)(pos - p0) : slot_at<QF>(h, cls, pos, false);
   } else if (req) {
     cell = ring_slot(h, cls, pos);
   }
@@ -1104,7 +1114,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, un
 
 template <int V, bool RESERVED = false>
 __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsigned vmask,
-                          unsigned long long t0_reserved = 0) {
+                          unsigned long long t_reserved = 0) {
   constexpr int QF = ouro_qform(V);
   constexpr bool VL = QF != OURO_QF_RING;
   ouro_qhdr *q = qh(h, cls);
@@ -1114,19 +1124,19 @@ __device__ void page_free(const ouro_heap_dev &h, int cls, unsigned item, unsign
   const unsigned rank = __popc(grp & lanemask_lt());
   unsigned long long t = 0;
   if (RESERVED) {
-    t = t0_reserved;   /* the caller took the group's tail positions and counted the frees */
+    t = t_reserved;    /* the caller took this lane's tail position and counted the frees */
   } else if (lane == leader) {
     t = atomicAdd(&q->tail.v, (unsigned long long)__popc(grp));
     stat_add(h, cls, OURO_ST_FREE, __popc(grp));
   }
-  const unsigned long long t0 = RESERVED ? t : __shfl_sync(vmask, t, leader);
-  t = t0 + rank;
+  const unsigned long long t0 = __shfl_sync(vmask, t, leader);   /* the group leader's position */
+  if (!RESERVED) t = t0 + rank;
   unsigned long long *cell;
   if (VL) {   /* the leader finds (or links) its segment; lanes in the same segment reuse it */
     unsigned long long *c0 = lane == leader ? slot_at<QF>(h, cls, t0, true) : nullptr;
     c0 = reinterpret_cast<unsigned long long *>(
         __shfl_sync(vmask, reinterpret_cast<unsigned long long>(c0), leader));
-    cell = (c0 && t / h.seg_cap == t0 / h.seg_cap) ? c0 + rank : slot_at<QF>(h, cls, t, true);
+    cell = (c0 && t / h.seg_cap == t0 / h.seg_cap) ? c0 + (long long)(t - t0) : slot_at<QF>(h, cls, t, true);
   } else {
     cell = ring_slot(h, cls, t);
   }

@@ -31,40 +31,94 @@ __global__ void k_batch_free(ouro_heap_dev h, void *const *ptrs, size_t n) {
     free_v<V>(h, ptrs[i]);
 }
 
-/* Block-aggregated forms (page queues, not the deoptimised form): the warps
- * of a block count their requests per class in shared memory, and one
- * thread per class takes the whole block's head (malloc) or tail (free)
- * positions with a single atomic, so the hot queue counters see one atomic
- * per class per block instead of one per class per warp.  Each warp then
- * serves its lanes from the reserved positions as the warp form does, and
- * the statistics are counted once per class per block. */
-template <int V>
-__global__ void __launch_bounds__(256) k_batch_malloc_blk(ouro_heap_dev h, const uint32_t *sizes, void **ptrs,
-                                                          size_t n) {
-  __shared__ unsigned long long s_cnt[OURO_MAX_CLASSES], s_pos[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
-  const unsigned lane = threadIdx.x & 31;
-  for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = base + threadIdx.x;
-    const bool act = i < n;
-    const uint32_t sz = act ? sizes[i] : 0;
-    const int cls = act ? size_class(h, sz) : -1;
-    if (act && cls < 0) stat_add(h, OURO_ROW_NONE, sz == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+/* Block-aggregated forms (page queues, not the deoptimised form): every
+ * request of a block takes its offset in its class's share with one
+ * shared-memory atomic, and one thread per class takes the whole block's
+ * head (malloc) or tail (free) positions with a single global atomic, so
+ * the hot queue counters see one atomic per class per block instead of one
+ * per class per warp.  Statistics are counted once per class per block.
+ *
+ * Each thread carries R requests (r * 256 + thread of the block's span, so
+ * loads coalesce).  On plain-array queues a thread first tries all R of its
+ * positions at once: R relaxed slot loads (malloc) or R relaxed slot CASes
+ * (free) in flight together, behind one acquire / release fence, instead of
+ * R chains of dependent round trips.  A position whose slot is not ready
+ * (not produced yet, or its previous lap not consumed yet) goes through the
+ * warp path with the position already taken, which waits, carves and
+ * answers as ouro_malloc / ouro_free do. */
+template <int R>
+__device__ __forceinline__ void blk_reserve(const int (&cls)[R], unsigned long long (&pos)[R], unsigned *s_cnt) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)   /* this request's offset in the block's share of its class */
+    pos[r] = cls[r] >= 0 ? atomicAdd(&s_cnt[cls[r]], 1u) : 0u;
+}
+
+template <int V, int R>
+__global__ void __launch_bounds__(256, 4) k_batch_malloc_blk(ouro_heap_dev h, const uint32_t *sizes, void **ptrs,
+                                                             size_t n) {
+  constexpr bool RING = ouro_qform(V) == OURO_QF_RING;
+  __shared__ unsigned s_cnt[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
+  __shared__ unsigned long long s_pos[OURO_MAX_CLASSES];
+  const size_t span = (size_t)blockDim.x * R;
+  for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
+    uint32_t sz[R];
+    int cls[R];
+    unsigned long long pos[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t i = base + (size_t)r * blockDim.x + threadIdx.x;
+      sz[r] = i < n ? sizes[i] : 0;
+    }
     if (threadIdx.x < OURO_MAX_CLASSES) s_cnt[threadIdx.x] = s_ok[threadIdx.x] = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const bool act = base + (size_t)r * blockDim.x + threadIdx.x < n;
+      cls[r] = act ? size_class(h, sz[r]) : -1;
+      if (act && cls[r] < 0) stat_add(h, OURO_ROW_NONE, sz[r] == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+    }
     __syncthreads();
-    const unsigned grp = __match_any_sync(0xffffffffu, cls);
-    const unsigned leader = __ffs(grp) - 1;
-    unsigned long long off = 0;
-    if (cls >= 0 && lane == leader) off = atomicAdd(&s_cnt[cls], (unsigned long long)__popc(grp));
+    blk_reserve<R>(cls, pos, s_cnt);
     __syncthreads();
     if (threadIdx.x < OURO_MAX_CLASSES && s_cnt[threadIdx.x])
-      s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->head.v, s_cnt[threadIdx.x]);
+      s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->head.v, (unsigned long long)s_cnt[threadIdx.x]);
     __syncthreads();
-    const unsigned long long p0 = __shfl_sync(0xffffffffu, cls >= 0 ? s_pos[cls] + off : 0ull, leader);
-    void *p = nullptr;
-    if (__any_sync(0xffffffffu, cls >= 0)) p = page_malloc<V, 1, true>(h, cls, 0xffffffffu, p0);
-    if (act) ptrs[i] = p;
-    const unsigned okm = __ballot_sync(0xffffffffu, p != nullptr) & grp;
-    if (cls >= 0 && lane == leader && okm) atomicAdd(&s_ok[cls], (unsigned long long)__popc(okm));
+    void *res[R];
+    bool pend[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (cls[r] >= 0) pos[r] += s_pos[cls[r]];
+      res[r] = nullptr;
+      pend[r] = cls[r] >= 0;
+    }
+    if (RING && !h.checked) {   /* fast path: every position's slot at once */
+      unsigned long long v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        v[r] = pend[r] && cls[r] < (int)h.n_classes ? ld_rlx(ring_slot(h, cls[r], pos[r])) : 0ull;
+      fence_acq_rel();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!pend[r] || cls[r] >= (int)h.n_classes) continue;
+        const int d = slot_d(v[r], pos[r]);
+        if (d == 1 || d == 2) {   /* an item, or the heap's null answer: take it, retire the slot */
+          st_rlx(ring_slot(h, cls[r], pos[r]), slot(pos[r] + h.ring_mask[cls[r]] + 1, 0));
+          if (d == 1) res[r] = h.base + ((size_t)lo32(v[r]) << (4 + cls[r]));
+          pend[r] = false;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {   /* the rest: the warp path from the taken positions */
+      if (!__any_sync(0xffffffffu, pend[r])) continue;
+      void *q = page_malloc<V, 1, true>(h, pend[r] ? cls[r] : -1, 0xffffffffu, pos[r]);
+      if (pend[r]) res[r] = q;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t i = base + (size_t)r * blockDim.x + threadIdx.x;
+      if (i < n) ptrs[i] = res[r];
+      if (res[r]) atomicAdd(&s_ok[cls[r]], 1u);
+    }
     __syncthreads();
     if (threadIdx.x < OURO_MAX_CLASSES && s_cnt[threadIdx.x]) {
       stat_add(h, threadIdx.x, OURO_ST_MALLOC, s_ok[threadIdx.x]);
@@ -74,30 +128,57 @@ __global__ void __launch_bounds__(256) k_batch_malloc_blk(ouro_heap_dev h, const
   }
 }
 
-template <int V>
+template <int V, int R>
 __global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *const *ptrs, size_t n) {
-  __shared__ unsigned long long s_cnt[OURO_MAX_CLASSES], s_pos[OURO_MAX_CLASSES];
-  const unsigned lane = threadIdx.x & 31;
-  for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = base + threadIdx.x;
-    void *p = i < n ? ptrs[i] : nullptr;
-    unsigned item = 0;
-    const int cls = free_locate<V>(h, p, item);
+  constexpr bool RING = ouro_qform(V) == OURO_QF_RING;
+  __shared__ unsigned s_cnt[OURO_MAX_CLASSES];
+  __shared__ unsigned long long s_pos[OURO_MAX_CLASSES];
+  const size_t span = (size_t)blockDim.x * R;
+  for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
+    void *p[R];
+    unsigned item[R];
+    int cls[R];
+    unsigned long long pos[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t i = base + (size_t)r * blockDim.x + threadIdx.x;
+      p[r] = i < n ? ptrs[i] : nullptr;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      item[r] = 0;
+      cls[r] = free_locate<V>(h, p[r], item[r]);
+    }
     if (threadIdx.x < OURO_MAX_CLASSES) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const unsigned grp = __match_any_sync(0xffffffffu, cls);
-    const unsigned leader = __ffs(grp) - 1;
-    unsigned long long off = 0;
-    if (cls >= 0 && lane == leader) off = atomicAdd(&s_cnt[cls], (unsigned long long)__popc(grp));
+    blk_reserve<R>(cls, pos, s_cnt);
     __syncthreads();
     if (threadIdx.x < OURO_MAX_CLASSES && s_cnt[threadIdx.x]) {
-      s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->tail.v, s_cnt[threadIdx.x]);
+      s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->tail.v, (unsigned long long)s_cnt[threadIdx.x]);
       stat_add(h, threadIdx.x, OURO_ST_FREE, s_cnt[threadIdx.x]);
     }
     __syncthreads();
-    const unsigned long long t0 = __shfl_sync(0xffffffffu, cls >= 0 ? s_pos[cls] + off : 0ull, leader);
-    const unsigned vmask = __ballot_sync(0xffffffffu, cls >= 0);
-    if (cls >= 0) page_free<V, true>(h, cls, item, vmask, t0);
+    bool pend[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (cls[r] >= 0) pos[r] += s_pos[cls[r]];
+      pend[r] = cls[r] >= 0;
+    }
+    if (RING) {   /* fast path: one release fence, then every slot's CAS at once */
+      unsigned long long old[R];
+      fence_acq_rel();
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        old[r] = pend[r] ? cas_rlx(ring_slot(h, cls[r], pos[r]), slot(pos[r], 0), slot(pos[r] + 1, item[r])) : 0ull;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (pend[r] && old[r] == slot(pos[r], 0)) pend[r] = false;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {   /* the rest: the warp path at the taken positions */
+      const unsigned vmask = __ballot_sync(0xffffffffu, pend[r]);
+      if (pend[r]) page_free<V, true>(h, cls[r], item[r], vmask, pos[r]);
+    }
     __syncthreads();
   }
 }
@@ -188,20 +269,31 @@ inline int grid_for(size_t n, int block, int cap) {
 namespace ouro {
 namespace launch {
 
+/* requests per thread of the block-aggregated kernels: several on plain
+ * arrays (their slots are tried together), one on virtualized queues */
+template <int V>
+constexpr int blk_reqs() { return ouro_qform(V) == OURO_QF_RING ? 4 : 1; }
+
 template <int V>
 ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n, cudaStream_t s) {
-  const int block = 256, g = grid_for(n, block, 1 << 20);
-  if (ouro_page_queues(V) && !H->d.deopt) k_batch_malloc_blk<V><<<g, block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
-  else k_batch_malloc<V><<<g, block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+  const int block = 256;
+  if (ouro_page_queues(V) && !H->d.deopt)
+    k_batch_malloc_blk<V, blk_reqs<V>()><<<grid_for((n + blk_reqs<V>() - 1) / blk_reqs<V>(), block, 1 << 20), block, 0,
+                                           s>>>(H->d, d_sizes, d_ptrs, n);
+  else
+    k_batch_malloc<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
   OURO_LAUNCHED();
   return OURO_OK;
 }
 
 template <int V>
 ouro_status batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, cudaStream_t s) {
-  const int block = 256, g = grid_for(n, block, 1 << 20);
-  if (ouro_page_queues(V) && !H->d.deopt) k_batch_free_blk<V><<<g, block, 0, s>>>(H->d, d_ptrs, n);
-  else k_batch_free<V><<<g, block, 0, s>>>(H->d, d_ptrs, n);
+  const int block = 256;
+  if (ouro_page_queues(V) && !H->d.deopt)
+    k_batch_free_blk<V, blk_reqs<V>()><<<grid_for((n + blk_reqs<V>() - 1) / blk_reqs<V>(), block, 1 << 20), block, 0,
+                                         s>>>(H->d, d_ptrs, n);
+  else
+    k_batch_free<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
   OURO_LAUNCHED();
   return OURO_OK;
 }
