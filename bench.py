@@ -79,8 +79,8 @@ def dist_env():
 # from the sources whose digest is recorded; null once they change.
 FUSED_KERNEL_SOURCES = ("include/ouro_device.cuh", "paper_2504_18211_gb300/csrc/ouro_payload.cuh",
                         "paper_2504_18211_gb300/csrc/ouro_kernels.cu", "paper_2504_18211_gb300/csrc/ouro_internal.cuh")
-FUSED_TRAFFIC = {"sources_sha256": "3b9ce6af25818d74906add0fa0f14c81c5b452ae2be7f4135fef6b88dbd9e79e",
-                 "bytes_per_launch": 1656264704}
+FUSED_TRAFFIC = {"sources_sha256": "e418543250fea85ae5a7085d1417fa91675891f4a48d25fb91e16cea27a1f4e0",
+                 "bytes_per_launch": 1656511488}
 
 
 def kernel_sources_digest() -> str:
@@ -398,7 +398,7 @@ def run_graph(args):
             ops = sum(st["mallocs"]) + sum(st["frees"]) - sum(st0["mallocs"])
             ok = (np.array_equal(deg, np.bincount(src, minlength=nv)) and st["mallocs"] == m.tolist()
                   and st["frees"] == f.tolist() and st["error_bits"] == 0 and g.ctl_dict()["failed"] == 0)
-            res[variant if form == "persistent" else f"{variant}_per_launch"] = {"form": form, "ms": round(ms, 2), "appends_per_s": round(ne / (ms / 1e3), 1),
+            res[variant] = {"ms": round(ms, 2), "appends_per_s": round(ne / (ms / 1e3), 1),
                             "alloc_ops": ops, "alloc_mops": round(ops / (ms / 1e3) / 1e6, 2),
                             "max_degree": int(deg.max()), "verified": bool(ok)}
             g.free(heap)
