@@ -269,19 +269,32 @@ inline int grid_for(size_t n, int block, int cap) {
 namespace ouro {
 namespace launch {
 
-/* requests per thread of the block-aggregated kernels: several on plain
- * arrays (their slots are tried together), one on virtualized queues */
-template <int V>
-constexpr int blk_reqs() { return ouro_qform(V) == OURO_QF_RING ? 4 : 1; }
+/* Requests per thread of the block-aggregated kernels: four on plain arrays
+ * (their slots are tried together) once a batch fills every SM with four
+ * per thread; one otherwise, and always on virtualized queues, so that a
+ * small batch still spreads over many blocks. */
+constexpr int BLK_WIDE = 4;
+inline bool blk_wide(size_t n) { return n >= (size_t)BLK_WIDE * 256 * ouro::host::sm_count(); }
 
 template <int V>
 ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n, cudaStream_t s) {
   const int block = 256;
-  if (ouro_page_queues(V) && !H->d.deopt)
-    k_batch_malloc_blk<V, blk_reqs<V>()><<<grid_for((n + blk_reqs<V>() - 1) / blk_reqs<V>(), block, 1 << 20), block, 0,
-                                           s>>>(H->d, d_sizes, d_ptrs, n);
-  else
-    k_batch_malloc<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+  if constexpr (ouro_page_queues(V)) {
+    if (!H->d.deopt) {
+      if constexpr (ouro_qform(V) == OURO_QF_RING) {
+        if (blk_wide(n)) {
+          k_batch_malloc_blk<V, BLK_WIDE><<<grid_for((n + BLK_WIDE - 1) / BLK_WIDE, block, 1 << 20), block, 0, s>>>(
+              H->d, d_sizes, d_ptrs, n);
+          OURO_LAUNCHED();
+          return OURO_OK;
+        }
+      }
+      k_batch_malloc_blk<V, 1><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+      OURO_LAUNCHED();
+      return OURO_OK;
+    }
+  }
+  k_batch_malloc<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
   OURO_LAUNCHED();
   return OURO_OK;
 }
@@ -289,11 +302,22 @@ ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, s
 template <int V>
 ouro_status batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, cudaStream_t s) {
   const int block = 256;
-  if (ouro_page_queues(V) && !H->d.deopt)
-    k_batch_free_blk<V, blk_reqs<V>()><<<grid_for((n + blk_reqs<V>() - 1) / blk_reqs<V>(), block, 1 << 20), block, 0,
-                                         s>>>(H->d, d_ptrs, n);
-  else
-    k_batch_free<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
+  if constexpr (ouro_page_queues(V)) {
+    if (!H->d.deopt) {
+      if constexpr (ouro_qform(V) == OURO_QF_RING) {
+        if (blk_wide(n)) {
+          k_batch_free_blk<V, BLK_WIDE><<<grid_for((n + BLK_WIDE - 1) / BLK_WIDE, block, 1 << 20), block, 0, s>>>(
+              H->d, d_ptrs, n);
+          OURO_LAUNCHED();
+          return OURO_OK;
+        }
+      }
+      k_batch_free_blk<V, 1><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
+      OURO_LAUNCHED();
+      return OURO_OK;
+    }
+  }
+  k_batch_free<V><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
   OURO_LAUNCHED();
   return OURO_OK;
 }
