@@ -57,3 +57,21 @@ def test_bad_arguments_are_rejected_on_the_host(lib_path):
     assert lib.ouro_heap_create(65 << 30, 1 << 20, C.byref(h)) == 1
     assert lib.ouro_heap_create_ex(1 << 20, 4096, 9, None, None, C.byref(h)) == 1
     assert lib.ouro_heap_destroy(None) == 0
+
+
+def test_every_kernel_source_is_built():
+    """Each .cu file of the package is compiled: whole, or once per queue
+    form plus once for its entry points (then it includes the shard header
+    and keeps its entry points behind OURO_SHARD_ENTRIES)."""
+    from paper_2504_18211_gb300 import build
+    csrc = os.path.join(ROOT, "paper_2504_18211_gb300", "csrc")
+    sources = sorted(f for f in os.listdir(csrc) if f.endswith(".cu"))
+    assert sorted(build.SOURCES + build.SHARDED) == sources
+    assert not set(build.SOURCES) & set(build.SHARDED)
+    for f in build.SHARDED:
+        text = open(os.path.join(csrc, f)).read()
+        assert '#include "ouro_shard.cuh"' in text, f
+        assert "OURO_SHARD_INSTANTIATE(" in text, f
+        first_entry = text.find('extern "C"')
+        assert first_entry > text.find("#if OURO_SHARD_ENTRIES") >= 0, f
+    assert len([j for j in build.JOBS if j[0] == build.SHARDED[0]]) == build.N_FORMS + 1
