@@ -201,12 +201,21 @@ ouro_status ouro_heap_stats(ouro_heap *h, ouro_stats *out, void *stream);
 ouro_status ouro_heap_snapshot(ouro_heap *h, ouro_snapshot *out, void *stream);
 void ouro_snapshot_free(ouro_snapshot *s);
 
-/* ---- batch API (one device thread per request) --------------------------- */
+/* ---- batch API --------------------------------------------------------------- */
 
-/* d_ptrs[i] = ouro_malloc(d_sizes[i]) for i < n; null for failures. */
+/* d_ptrs[i] = ouro_malloc(d_sizes[i]) for i < n; null for failures.  The
+ * results, counters and queue states are those of n ouro_malloc calls (the
+ * class queues of Sec. 4.1-4.3).  On page queues the kernel takes the head
+ * positions of a whole block of requests with one atomic per class, and on
+ * plain arrays a batch of at least 4 x 256 x (SM count) requests runs four
+ * requests per thread with their slots read together; chunk queues and the
+ * deoptimised form take one atomic per warp class group, as ouro_malloc. */
 ouro_status ouro_batch_malloc(ouro_heap *h, const uint32_t *d_sizes, void **d_ptrs, size_t n,
                               void *stream);
-/* ouro_free(d_ptrs[i]) for i < n; null entries are skipped. */
+/* ouro_free(d_ptrs[i]) for i < n; null entries are skipped.  Aggregated like
+ * ouro_batch_malloc: tail positions per class and block on page queues,
+ * four requests per thread with their slot writes together on plain arrays
+ * for large batches. */
 ouro_status ouro_batch_free(ouro_heap *h, void *const *d_ptrs, size_t n, void *stream);
 
 /* ---- driver round payload (Sec. 3: write data, read it back, check) ------ */
