@@ -789,19 +789,28 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
         t_dist = n / rates[2]                           # one slot CAS per free
         return n / (t_same + t_dist), g
 
-    roof_pairs, g_blk = roof_pairs_for(256)             # the batch kernels aggregate per block of 256
+    # the batch kernels on page queues aggregate per block: 256 threads, four
+    # requests each on plain arrays once a batch fills every SM that way (as
+    # the library does); chunk queues aggregate per warp
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if args.variant.startswith("page_"):
+        span = 256 * (4 if args.variant == "page_array" and n >= 4 * 256 * sms else 1)
+    else:
+        span = 32
+    roof_pairs, g_blk = roof_pairs_for(span)
     warp_pairs, g_warp = roof_pairs_for(32)
     ach_pairs = n / (af / 1e3)
     ex["atomic_roofline"] = {
         "rates_gops": {"same_address": round(rates[0] / 1e9, 3), "32_addresses": round(rates[1] / 1e9, 3),
                        "distinct_cas": round(rates[2] / 1e9, 3)},
-        "classes_per_block": round(g_blk, 2), "classes_per_warp": round(g_warp, 2),
+        "block_span": span, "classes_per_block": round(g_blk, 2), "classes_per_warp": round(g_warp, 2),
         "roofline_mops": round(2 * roof_pairs / 1e6, 1),
         "achieved_mops": round(2 * ach_pairs / 1e6, 1), "frac": round(ach_pairs / roof_pairs, 4),
         "warp_aggregated_roofline_mops": round(2 * warp_pairs / 1e6, 1),
-        "model": "per malloc+free pair: one same-address atomic per block class group (256 requests) on head "
-                 "and on tail (busiest class serialises), one distinct-address slot CAS per free; per-launch "
-                 "timings. warp_aggregated_roofline_mops: the same bound with one atomic per warp class group"}
+        "model": "per malloc+free pair: one same-address atomic per block class group (block_span requests) "
+                 "on head and on tail (busiest class serialises), one distinct-address slot CAS per free; "
+                 "per-launch timings. warp_aggregated_roofline_mops: the same bound with one atomic per warp "
+                 "class group"}
     return ex
 
 
