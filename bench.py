@@ -323,7 +323,8 @@ def run_serving(args):
     import paper_2504_18211_gb300 as P
     from paper_2504_18211_gb300 import build as B
     from paper_2504_18211_gb300 import workloads as W
-    from paper_2504_18211_gb300.serving import ServeRun, model_schedule
+    from oracle.patterns import serving_schedule
+    from paper_2504_18211_gb300.serving import ServeRun
     B.build()
     P.load()
     steps, block, heap_bytes = 2000, 16384, 64 << 30
@@ -337,7 +338,7 @@ def run_serving(args):
             ms = run.run(heap, cap, form=form)
             r = run.results()
             st = heap.stats()
-        admit, done, _ = model_schedule(arrive, blocks, steps, 16384, cap)
+        admit, done, _ = serving_schedule(arrive, blocks, steps, 16384, cap)
         fin = np.flatnonzero(done >= 0)
         sample = fin[:: max(1, fin.size // 64)]
         ok = all((int(r["xor"][s]), int(r["sum"][s])) == (
@@ -373,7 +374,8 @@ def run_graph(args):
     import paper_2504_18211_gb300 as P
     from paper_2504_18211_gb300 import build as B
     from paper_2504_18211_gb300 import workloads as W
-    from paper_2504_18211_gb300.graph import GraphRun, expected_class_counts
+    from oracle.patterns import graph_class_counts
+    from paper_2504_18211_gb300.graph import GraphRun
     B.build()
     P.load()
     nv, ne, chunk, heap_bytes = 1 << 20, 1 << 24, 8192, 16 << 30
@@ -394,7 +396,7 @@ def run_graph(args):
             ms = a.elapsed_time(b)
             st = heap.stats()
             deg = g.degrees()
-            m, f, _ = expected_class_counts(deg, chunk, heap.n_classes)
+            m, f, _ = graph_class_counts(deg, chunk, heap.n_classes)
             ops = sum(st["mallocs"]) + sum(st["frees"]) - sum(st0["mallocs"])
             ok = (np.array_equal(deg, np.bincount(src, minlength=nv)) and st["mallocs"] == m.tolist()
                   and st["frees"] == f.tolist() and st["error_bits"] == 0 and g.ctl_dict()["failed"] == 0)

@@ -245,10 +245,11 @@ ouro_status ouro_round_fused(ouro_heap *h, const uint32_t *d_sizes, size_t n, ui
                              int mode, ouro_check *d_out, void **d_ptrs, void *stream);
 
 /* Same result as ouro_heap_stats, for callers that cannot allocate device
- * memory when they ask: code running while a CUDA stream capture is open
- * (cudaMalloc is not allowed there) or applications whose device memory is
- * all handed out up front by their own pool.  The paper has no counterpart;
- * this is a service of this library.
+ * memory when they ask: applications whose device memory is all handed out
+ * up front by their own pool (a cudaMalloc would fail, or take memory the
+ * pool counts on), and latency-bound loops that must not let a cudaMalloc /
+ * cudaFree stall the device while other streams are busy.  The paper has no
+ * counterpart; this is a service of this library.
  *   - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  *     call.  Its scratch (1584 bytes) is a file-scope __device__ array that
  *     every GPU loading the library keeps until the process exits.

@@ -201,16 +201,25 @@ class OracleHeap:
 
     # --- driver round ----------------------------------------------------
     def round(self, sizes: np.ndarray, seed: int, mode: int = 1, with_memory: bool = True,
-              return_offsets: bool = False):
+              return_offsets: bool = False, return_memory: bool = False):
+        """One driver round (Sec. 3) over `sizes`: allocate all, write, read
+        back and check, free all.  Returns the checksum dict; with
+        return_offsets / return_memory also the block offsets and the heap
+        bytes as the round left them (host memory, zero where never written)."""
         sizes = np.ascontiguousarray(sizes, dtype=np.uint32)
         n = sizes.size
-        mem = np.zeros(self.bytes, np.uint8) if with_memory else None
-        offs = np.zeros(max(n, 1), np.int64) if return_offsets else None
+        mem = np.zeros(self.bytes, np.uint8) if (with_memory or return_memory) else None
+        offs = np.zeros(max(n, 1), np.int64) if (return_offsets or return_memory) else None
         r = RoundResult()
         self.lib.orc_round(self.h, _ptr(sizes), n, seed, mode,
                            _ptr(mem) if mem is not None else None,
                            _ptr(offs) if offs is not None else None, C.byref(r))
-        return (r.as_dict(), offs[:n]) if return_offsets else r.as_dict()
+        out = [r.as_dict()]
+        if return_offsets or return_memory:
+            out.append(offs[:n])
+        if return_memory:
+            out.append(mem)
+        return tuple(out) if len(out) > 1 else out[0]
 
 
 def expected_checksums(sizes: np.ndarray, seed: int, mode: int = 1) -> dict:

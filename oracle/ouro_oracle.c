@@ -130,7 +130,7 @@ orc_heap *orc_create(uint64_t bytes, uint64_t chunk_bytes, int variant, uint64_t
   h->n_chunks = bytes / chunk_bytes;
   h->variant = variant;
   h->n_classes = orc_num_classes(chunk_bytes);
-  h->queue_cap = queue_cap ? queue_cap : (1ull << 24);
+  h->queue_cap = queue_cap ? queue_cap : (1ull << 23);
   /* a segment is one chunk: a 64-byte header, then 8-byte cells */
   h->seg_cap = (chunk_bytes - 64) / 8;
   h->words_per_chunk = (chunk_bytes / 16 + 63) / 64;

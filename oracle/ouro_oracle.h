@@ -65,7 +65,7 @@ typedef struct {
 } orc_stats;
 
 /* chunk_bytes: power of two in [256, 1 MiB]; bytes: multiple of chunk_bytes.
- * queue_cap: per-class item limit of page-array queues (0 = default 2^24).
+ * queue_cap: per-class item limit of page-array queues (0 = default 2^23).
  * Returns NULL on a bad argument or when host memory runs out. */
 orc_heap *orc_create(uint64_t bytes, uint64_t chunk_bytes, int variant, uint64_t queue_cap);
 void      orc_destroy(orc_heap *h);

@@ -793,11 +793,11 @@ extern "C" ouro_status ouro_debug_stall_producer(ouro_heap *H, int cls, uint32_t
 
 /* ------------------------------------------- statistics without allocation */
 /* For callers that must not allocate device memory at the time they ask for
- * statistics, e.g. code running while a CUDA stream capture is open (where
- * cudaMalloc is not permitted) or applications whose device memory is all
- * handed out up front by their own pool.  The scratch lives in this file-scope
- * device array instead of a cudaMalloc'ed buffer; every device that loads the
- * library holds it (1.5 KiB) until the process exits. */
+ * statistics: applications whose device memory is all handed out up front by
+ * their own pool, and latency-bound loops in which a cudaMalloc / cudaFree
+ * could stall the device.  The scratch lives in this file-scope device array
+ * instead of a cudaMalloc'ed buffer; every device that loads the library
+ * holds it (1.5 KiB) until the process exits. */
 #define OURO_STATIC_SCRATCH_ROWS (OURO_MAX_CLASSES + 1)
 #define OURO_STATIC_SCRATCH_WORDS (OURO_STATIC_SCRATCH_ROWS * (OURO_NSTAT + 3))
 static __device__ __align__(256) unsigned long long g_stats_scratch[OURO_STATIC_SCRATCH_WORDS];

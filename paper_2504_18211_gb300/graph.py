@@ -57,31 +57,3 @@ class GraphRun:
         c = self.ctl.cpu().numpy()
         return {"appended": int(c[0]), "failed": int(c[1]), "skipped": int(c[2])}
 
-
-def expected_class_counts(deg: np.ndarray, chunk_bytes: int, n_classes: int) -> tuple:
-    """Closed form of the allocator traffic of the growth rule, from the final
-    degrees alone: one 16 B list per vertex; every doubling from 4 entries up
-    to min(next power of two >= degree, one chunk) is a malloc of the new size
-    and a free of the old; entries past one chunk take one chunk-size
-    segment per (chunk - 8) / 4 entries."""
-    max_plain = chunk_bytes // 4
-    seg_cap = (chunk_bytes - 8) // 4
-    mallocs = np.zeros(n_classes, np.int64)
-    frees = np.zeros(n_classes, np.int64)
-    mallocs[0] += deg.size
-    plain = np.minimum(deg.astype(np.int64), max_plain)
-    cap = np.full(deg.size, 4, np.int64)
-    while True:
-        grow = plain > cap
-        if not grow.any():
-            break
-        old_cls = np.log2(cap[grow] * 4).astype(np.int64) - 4
-        new_cls = old_cls + 1
-        np.add.at(frees, old_cls, 1)
-        np.add.at(mallocs, new_cls, 1)
-        cap[grow] *= 2
-    over = np.maximum(deg.astype(np.int64) - max_plain, 0)
-    mallocs[n_classes - 1] += int(((over + seg_cap - 1) // seg_cap).sum())
-    # the heap reports every class up to 1 MiB (runs of chunks above n_classes): none used here
-    pad = np.zeros(max(0, 17 - n_classes), np.int64)
-    return np.concatenate([mallocs, pad]), np.concatenate([frees, pad]), cap

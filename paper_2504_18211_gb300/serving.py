@@ -71,31 +71,3 @@ class ServeRun:
                 "mallocs": int(ctl[5]), "frees": int(ctl[6]), "failed": int(ctl[7]), "error": int(ctl[4]),
                 "step_us": lat, "phases": phases}
 
-
-def model_schedule(arrive: np.ndarray, blocks: np.ndarray, steps: int, n_slots: int, cap_blocks: int):
-    """Host restatement of the admission rule for checking the device loop:
-    arrival order, a free slot, committed blocks + newcomer <= cap; every
-    active session grows one block per step; a session completes (and frees)
-    in the step in which it reaches its size."""
-    n = arrive.size
-    admit = np.full(n, -1, np.int64)
-    done = np.full(n, -1, np.int64)
-    k = np.zeros(n, np.int64)
-    active, nxt, committed = [], 0, 0
-    for step in range(steps):
-        while nxt < n and arrive[nxt] <= step and committed + int(blocks[nxt]) <= cap_blocks and \
-                len(active) < n_slots:
-            admit[nxt] = step
-            committed += int(blocks[nxt])
-            active.append(nxt)
-            nxt += 1
-        keep = []
-        for s in active:
-            k[s] += 1
-            if k[s] >= blocks[s]:
-                done[s] = step
-                committed -= int(blocks[s])
-            else:
-                keep.append(s)
-        active = keep
-    return admit, done, k

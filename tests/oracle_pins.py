@@ -16,9 +16,16 @@ What pins what:
   restore            free everything, trim: the state equals the post-create state
   queue segments     closed form of segment use for a fill that ends on a segment edge
   fmix32             MurmurHash3 reference vectors (tests/golden/murmur3_fmix32.json)
+  written data       hand-worked words, tail bytes and checksums of the driver round
+                     (tests/golden/pattern_words.json)
+  default capacity   the page-array limit at default options is the documented 2^23
+  serving admission  hand-worked schedules (binding cap, full slot table, late arrival)
+  graph growth       hand-worked per-class counts, and the rule run request by request
+                     on the oracle heap
 """
 from __future__ import annotations
 
+import ctypes
 import itertools
 import json
 import os
@@ -116,6 +123,14 @@ def pin_capacity(lib_path):
         again = [h.malloc(2049) for _ in range(16)]         # 2049 B: the same class
         assert again == offs[15::-1], (variant, again)
         assert h.stats()["bump"] == 64 and h.malloc(16) == -1
+    # the page-array limit at default options is the library's documented
+    # default, 2^23 items per class (include/ouro.h): a 256 MiB heap holds
+    # 2^24 pages of 16 B, of which exactly 2^23 are served
+    h = heap(lib_path, 256 << 20, 8192, "page_array")
+    res = h.round(np.full((1 << 23) + 1000, 16, np.uint32), seed=0, mode=1, with_memory=False)
+    assert res["nulls"] == 1000, res
+    st = h.stats()
+    assert st["mallocs"][0] == 1 << 23 and st["failed"][0] == 1000 and st["carves"][0] == (1 << 23) // 512, st
 
 
 def _run_sequence(lib_path, variant, bytes_, chunk, ops, model_nulls=True):
@@ -293,6 +308,103 @@ def pin_segments(lib_path):
         assert (st["seg_chunks"], st["spare_chunks"], st["bump"]) == after56, (variant, st)
 
 
+def pin_pattern(lib_path):
+    """The written data of the driver round against the hand-worked cases of
+    tests/golden/pattern_words.json (keys from the MurmurHash3 vectors):
+    the words of mode 1, the tail bytes of sizes that are not a multiple of
+    4 (the low bytes of the next word, little-endian), the XOR / sum folds
+    of the checksum, the bytes the round leaves in memory, and mode 0's
+    thread id in word 0."""
+    lib = oracle.load(lib_path)
+    g = json.load(open(os.path.join(GOLDEN, "pattern_words.json")))
+    gold = int(g["gold"], 16)
+    for c in g["mode1"]:
+        seed, tid, key, size = int(c["seed"], 16), c["tid"], int(c["key"], 16), c["size"]
+        want = bytes.fromhex(c["bytes"])
+        assert len(want) == size
+        for i in range(size // 4):
+            assert lib.orc_pattern_word(seed, tid, i, 1) == int.from_bytes(want[4 * i:4 * i + 4], "little"), c
+        assert lib.orc_pattern_word(seed, tid, 0, 1) == key, c
+        assert lib.orc_pattern_word(seed, tid, 5, 1) == (key + 5 * gold) & 0xFFFFFFFF, c
+        sizes = np.array([size] if tid == 0 else [0] * tid + [size], np.uint32)
+        exp = {"xor64": c["xor64"], "sum64": c["sum64"], "words": c["words"]}
+        r = oracle.RoundResult()
+        lib.orc_expected_checksums(sizes.ctypes.data_as(ctypes.c_void_p), sizes.size, seed, 1, ctypes.byref(r))
+        assert {k: v for k, v in r.as_dict().items() if k in exp} == exp, (c, r.as_dict())
+        h = heap(lib_path, 1 << 16, 1024, "page_array")
+        res, offs, mem = h.round(sizes, seed=seed, mode=1, return_memory=True)
+        assert res["mismatches"] == 0 and res["nulls"] == tid, (c, res)
+        assert {k: v for k, v in res.items() if k in exp} == exp, (c, res)
+        o = int(offs[tid])
+        assert bytes(mem[o:o + size]) == want, (c, bytes(mem[o:o + size]).hex())
+        assert not mem[o + size:o + 16 * ((size + 15) // 16)].any()     # nothing past the request
+    m0 = g["mode0"]
+    sizes = np.array(m0["sizes"], np.uint32)
+    h = heap(lib_path, 1 << 16, 1024, "page_array")
+    res, offs, mem = h.round(sizes, seed=int(m0["seed"], 16), mode=0, return_memory=True)
+    assert (res["xor64"], res["sum64"], res["words"], res["mismatches"]) == (m0["xor64"], m0["sum64"], m0["words"], 0)
+    for t, o in enumerate(offs):
+        assert int.from_bytes(bytes(mem[o:o + 4]), "little") == m0["word0"][t] and not mem[o + 4:o + 16].any()
+
+
+def _patterns(mod):
+    if mod is None:
+        from oracle import patterns as mod
+    return mod
+
+
+def pin_serving_schedule(lib_path, mod=None):
+    """The serving admission rule against hand-worked schedules.
+    (a) 2 slots, cap 10 blocks; sessions (arrive, blocks) = (0,3) (0,4)
+        (0,5) (1,2).  Step 0 admits s0, s1 (7 committed); s2 would make 12
+        and blocks s3 behind it.  s0 completes at step 2 (4 committed); at
+        step 3 s2 fits (9) and s1 completes (5); at step 4 s3 fits (7);
+        s3 completes at step 5, s2 at step 7.
+    (b) 1 slot, cap 100: (0,2) (0,1): s1 waits for the slot; s0 completes
+        at step 1, s1 is admitted at step 2 and completes there.
+    (c) a late arrival (5,1) is admitted at step 5; a session larger than
+        the cap is never admitted and blocks every later one.
+    (d) (0,4) (0,6) under cap 10 fill it exactly: both are admitted at 0.
+    (e) sessions still growing at the last step have no completion."""
+    m = _patterns(mod)
+    a, d, k = m.serving_schedule(np.array([0, 0, 0, 1]), np.array([3, 4, 5, 2]), 10, 2, 10)
+    assert a.tolist() == [0, 0, 3, 4] and d.tolist() == [2, 3, 7, 5] and k.tolist() == [3, 4, 5, 2], (a, d, k)
+    a, d, k = m.serving_schedule(np.array([0, 0]), np.array([2, 1]), 4, 1, 100)
+    assert a.tolist() == [0, 2] and d.tolist() == [1, 2], (a, d)
+    a, d, k = m.serving_schedule(np.array([5, 5, 6]), np.array([1, 11, 1]), 9, 4, 10)
+    assert a.tolist() == [5, -1, -1] and d.tolist() == [5, -1, -1] and k.tolist() == [1, 0, 0], (a, d, k)
+    a, d, k = m.serving_schedule(np.array([0, 0]), np.array([4, 6]), 8, 4, 10)     # exactly at the cap
+    assert a.tolist() == [0, 0] and d.tolist() == [3, 5], (a, d)
+    a, d, k = m.serving_schedule(np.array([0, 0]), np.array([3, 3]), 2, 4, 10)
+    assert a.tolist() == [0, 0] and d.tolist() == [-1, -1] and k.tolist() == [2, 2], (a, d, k)
+
+
+def pin_graph_counts(lib_path, mod=None):
+    """The list-growth rule's allocator traffic against a hand-worked case
+    and against the same rule run request by request on an oracle heap.
+    Hand-worked, 256 B chunks (lists up to 64 entries, overflow segments of
+    (256 - 8) / 4 = 62 entries, 5 classes 16..256 B), final degrees 0, 4, 5,
+    9, 64, 65, 200: seven 16 B lists; doublings 4->8 for degrees 5, 9, 64,
+    65, 200, 8->16 for 9 and up, 16->32 and 32->64 for 64 and up; overflow
+    segments 0 + 1 + ceil(136 / 62) = 4 more 256 B blocks."""
+    m = _patterns(mod)
+    deg = np.array([0, 4, 5, 9, 64, 65, 200])
+    mal, fre, cap = m.graph_class_counts(deg, 256, 5)
+    assert mal[:5].tolist() == [7, 5, 4, 3, 3 + 4] and not mal[5:].any(), mal
+    assert fre[:5].tolist() == [5, 4, 3, 3, 0] and not fre[5:].any(), fre
+    assert cap.tolist() == [4, 4, 8, 16, 64, 64, 64], cap
+    # the rule run edge by edge on the oracle heap (its own counters)
+    rng = np.random.default_rng(11)
+    for chunk, nv, ne in ((256, 40, 3000), (1024, 64, 6000)):
+        src = (rng.zipf(1.6, ne) - 1) % nv
+        h = heap(lib_path, 4 << 20, chunk, "page_array")
+        st, d = m.graph_growth_run(h, src, nv, chunk)
+        assert d.max() > chunk // 4 + (chunk - 8) // 4          # several overflow segments
+        mal, fre, _ = m.graph_class_counts(d, chunk, h.n_classes)
+        assert st["mallocs"] == mal[:len(st["mallocs"])].tolist(), (chunk, st["mallocs"], mal)
+        assert st["frees"] == fre[:len(st["frees"])].tolist(), (chunk, st["frees"], fre)
+
+
 def pin_fmix32(lib_path):
     lib = oracle.load(lib_path)
     g = json.load(open(os.path.join(GOLDEN, "murmur3_fmix32.json")))
@@ -301,4 +413,4 @@ def pin_fmix32(lib_path):
 
 
 ALL_PINS = (pin_class_map, pin_layout, pin_capacity, pin_brute_force, pin_small_workload,
-            pin_restore, pin_segments, pin_fmix32)
+            pin_restore, pin_segments, pin_fmix32, pin_pattern, pin_serving_schedule, pin_graph_counts)

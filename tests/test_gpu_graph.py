@@ -8,6 +8,7 @@ list and trimming gives the post-create state."""
 import numpy as np
 import pytest
 
+from oracle.patterns import graph_class_counts
 from gpu_helpers import same_canonical_as_post_create, torch_cuda
 from paper_2504_18211_gb300 import workloads as W
 
@@ -25,7 +26,7 @@ def P():
 
 @pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray"])
 def test_graph_growth_matches_edge_list_and_closed_form(P, variant):
-    from paper_2504_18211_gb300.graph import GraphRun, expected_class_counts
+    from paper_2504_18211_gb300.graph import GraphRun
     torch = torch_cuda()
     nv, ne, chunk = 4096, 1 << 17, 8192
     src, dst = W.graph_workload(n_vertices=nv, n_edges=ne, seed=W.SEED_BASE + 51)
@@ -45,7 +46,7 @@ def test_graph_growth_matches_edge_list_and_closed_form(P, variant):
         order = np.lexsort((dst, src))
         assert np.array_equal(out[got], dst[order])
         st = heap.stats()
-        m, f, _ = expected_class_counts(deg, chunk, heap.n_classes)
+        m, f, _ = graph_class_counts(deg, chunk, heap.n_classes)
         assert st["mallocs"] == m.tolist() and st["frees"] == f.tolist()
         assert st["error_bits"] == 0
         g.free(heap)

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle.patterns import serving_schedule
 from gpu_helpers import torch_cuda
 from paper_2504_18211_gb300 import workloads as W
 
@@ -31,7 +32,7 @@ def session_checksum(seed, s, nblocks, block_bytes):
 
 @pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray"])
 def test_serving_loop_matches_model_and_oracle(P, variant):
-    from paper_2504_18211_gb300.serving import ServeRun, model_schedule
+    from paper_2504_18211_gb300.serving import ServeRun
     torch_cuda()
     steps, block = 300, 16384
     arrive, blocks = W.serving_workload(steps=steps, rate=2000.0, dt=0.01, median_bytes=256 << 10, sigma=1.0,
@@ -44,7 +45,7 @@ def test_serving_loop_matches_model_and_oracle(P, variant):
         r = run.results()
         st = heap.stats()
     assert r["error"] == 0 and r["failed"] == 0 and st["error_bits"] == 0
-    admit, done, k = model_schedule(arrive, blocks, steps, 1024, cap)
+    admit, done, k = serving_schedule(arrive, blocks, steps, 1024, cap)
     assert np.array_equal(r["admit"], admit)
     assert np.array_equal(r["done"], done)
     assert (done >= 0).sum() > 50 and (admit < 0).sum() > 0          # completions and a binding cap
@@ -71,7 +72,7 @@ def test_serving_per_launch_form_equals_loop(P, variant):
     """The per-launch form (four launches per step) gives the loop's results:
     the same admission schedule (the host model's), the same per-session
     checksums and mismatch counts, the same allocator counts."""
-    from paper_2504_18211_gb300.serving import ServeRun, model_schedule
+    from paper_2504_18211_gb300.serving import ServeRun
     torch_cuda()
     steps, block = 200, 16384
     arrive, blocks = W.serving_workload(steps=steps, rate=2000.0, dt=0.01, median_bytes=256 << 10, sigma=1.0,
@@ -89,7 +90,7 @@ def test_serving_per_launch_form_equals_loop(P, variant):
         assert sum(st["live"]) == r["mallocs"] - r["frees"], form
         assert np.all(np.diff(run.step_ns.cpu().numpy().reshape(-1, 3)[:, 2]) >= 0), form   # stamps in order
         got[form] = r
-    admit, done, k = model_schedule(arrive, blocks, steps, 512, cap)
+    admit, done, k = serving_schedule(arrive, blocks, steps, 512, cap)
     a, b = got["persistent"], got["per_launch"]
     assert (done >= 0).sum() > 30 and (admit < 0).sum() > 0
     for r in (a, b):

@@ -16,6 +16,7 @@ import oracle
 import oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "ouro_oracle.c")
+PY_SRC = os.path.join(os.path.dirname(oracle.__file__), "patterns.py")
 
 MUTANTS = {
     "class_off_by_one": ("while (orc_page_bytes(c) < n) c++;", "while (orc_page_bytes(c) <= n) c++;"),
@@ -42,6 +43,19 @@ MUTANTS = {
     "run_overlaps_next": ("  h->bump += k;", "  h->bump += 1;"),
     "trim_keeps_free_runs": ("        h->chunk_cls[x + j] = CLS_NONE;", ""),
     "run_double_free_missed": ("    if (c >= CLS_RUN_FREE) { h->err |= ORC_ERR_DOUBLE_FREE; return ORC_ERR_DOUBLE_FREE; }", ""),
+    "default_cap_2_24": ("h->queue_cap = queue_cap ? queue_cap : (1ull << 23);",
+                         "h->queue_cap = queue_cap ? queue_cap : (1ull << 24);"),
+    "pattern_key_without_gold": ("uint32_t key = orc_fmix32(seed ^ (tid * 0x9E3779B9u));",
+                                 "uint32_t key = orc_fmix32(seed ^ tid);"),
+    "pattern_step_dropped": ("return key + i * 0x9E3779B9u;", "return key + i;"),
+    "pattern_mode0_off": ("if (mode == 0) return tid;", "if (mode == 0) return tid + 1;"),
+    "tail_written_from_high_end": ("for (uint64_t j = 0; j < tail; j++) b[4 * nw + j] = (uint8_t)(v >> (8 * j));",
+                                   "for (uint64_t j = 0; j < tail; j++) b[4 * nw + j] = (uint8_t)(v >> (24 - 8 * j));"),
+    "tail_checked_from_high_end": ("uint8_t wb = (uint8_t)(v >> (8 * j));", "uint8_t wb = (uint8_t)(v >> (24 - 8 * j));"),
+    "tail_folded_from_high_end": ("fold(res, v & (uint32_t)((1ull << (8 * tail)) - 1));",
+                                  "fold(res, v >> (8 * (4 - tail)));"),
+    "tail_word_index": ("uint32_t v = orc_pattern_word(seed, (uint32_t)t, (uint32_t)nw, 1);\n      fold(",
+                        "uint32_t v = orc_pattern_word(seed, (uint32_t)t, (uint32_t)nw - 1, 1);\n      fold("),
 }
 
 
@@ -89,3 +103,49 @@ def test_mutant_is_caught(name):
         lib = _build_mutant(name, old, new, d)
         caught = next((p.__name__ for p in P.ALL_PINS if _pin_fails(p.__name__, lib)), None)
         assert caught, f"mutant {name} passed every pin"
+
+
+# planted mistakes in the oracle of the added patterns (oracle/patterns.py);
+# each must fail its pin (run in a child process against the mutated module)
+PY_MUTANTS = {
+    "admit_overtakes": ("                break\n            admit[nxt] = step",
+                        "                nxt += 1\n                continue\n            admit[nxt] = step", "pin_serving_schedule"),
+    "admit_ignores_slots": (" or len(active) >= n_slots:", ":", "pin_serving_schedule"),
+    "admit_cap_strict": ("committed + need > cap_blocks", "committed + need >= cap_blocks", "pin_serving_schedule"),
+    "complete_one_late": ("if grown[s] >= int(blocks[s]):", "if grown[s] > int(blocks[s]):", "pin_serving_schedule"),
+    "complete_keeps_blocks": ("                committed -= int(blocks[s])\n", "", "pin_serving_schedule"),
+    "growth_stops_early": ("while cap < min(d, max_plain):", "while cap < min(d, max_plain // 2):", "pin_graph_counts"),
+    "growth_frees_new_class": ("frees[_class_of_entries(cap)] += 1\n            cap *= 2",
+                               "cap *= 2\n            frees[_class_of_entries(cap)] += 1", "pin_graph_counts"),
+    "segment_without_link": ("    seg_cap = (chunk_bytes - 8) // 4\n    mallocs =", "    seg_cap = chunk_bytes // 4\n    mallocs =",
+                             "pin_graph_counts"),
+    "segments_floor": ("(over + seg_cap - 1) // seg_cap", "over // seg_cap", "pin_graph_counts"),
+}
+
+_PY_RUNNER = """
+import importlib.util, sys
+sys.path[:0] = [{root!r}, {tests!r}]
+import oracle, oracle_pins as P
+spec = importlib.util.spec_from_file_location("mutant_patterns", {path!r})
+mod = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(mod)
+getattr(P, {pin!r})(oracle.ensure_built(), mod)
+"""
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pattern_mutant_is_caught(name):
+    old, new, pin = PY_MUTANTS[name]
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    tests = os.path.dirname(os.path.abspath(__file__))
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "patterns_mutant.py")
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+        code = _PY_RUNNER.format(root=os.path.dirname(tests), tests=tests, path=path, pin=pin)
+        try:
+            r = subprocess.run([sys.executable, "-c", code], capture_output=True, timeout=120)
+        except subprocess.TimeoutExpired:
+            return
+        assert r.returncode != 0, f"mutant {name} passed {pin}"

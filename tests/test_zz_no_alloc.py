@@ -1,8 +1,9 @@
 """ouro_heap_stats_static: statistics for callers that cannot allocate device memory.
 
-Some callers cannot call cudaMalloc when they want the heap's counters: code
-running while a CUDA stream capture is open, or applications whose device
-memory is all handed out up front by their own pool.  ouro_heap_stats_static
+Some callers cannot call cudaMalloc when they want the heap's counters:
+applications whose device memory is all handed out up front by their own
+pool, or latency-bound loops in which a cudaMalloc / cudaFree could stall the
+device while other streams work.  ouro_heap_stats_static
 gives the same result as ouro_heap_stats with its scratch in a static device
 array.  This file is collected last (tests/test_zz_*) so that a failure here
 leaves every other test already run; it passes alone and after the others.
