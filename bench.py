@@ -201,188 +201,267 @@ def classes_per_group(sizes, width):
 
 
 # ---------------------------------------------------------------- CPU arm
-def cpu_oracle_sample(seconds: float, seed: int = SEED):
-    """The sequential oracle on a bounded sample of the same workload:
-    2^16 requests of the same size distribution on a 1 GiB heap (payload
-    written to host memory), rounds repeated for about `seconds`."""
-    import numpy as np
+def host_cpu() -> dict:
+    """The host's logical CPU count and CPU model (x86: "model name"; Arm:
+    lscpu's model name, else the implementer / part codes of /proc/cpuinfo)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            info = {}
+            for line in open("/proc/cpuinfo"):
+                if ":" in line:
+                    k, v = (x.strip() for x in line.split(":", 1))
+                    info.setdefault(k, v)
+            model = info.get("model name") or \
+                f"CPU implementer {info.get('CPU implementer', '?')} part {info.get('CPU part', '?')}"
+        except OSError:
+            model = "unknown"
+    return {"host_cpus": os.cpu_count(), "cpu_model": model}
 
-    import oracle
-    from paper_2504_18211_gb300 import workloads as W
-    n = 1 << 16
-    sizes = W.sweep_sizes(n)
-    h = oracle.OracleHeap(1 << 30, CHUNK, "page_array")
-    mem = np.zeros(1 << 30, np.uint8)
-    lib, r = h.lib, oracle.RoundResult()
-    import ctypes as C
-    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
-    lib.orc_round(h.h, ptr(sizes), n, seed, 1, ptr(mem), None, C.byref(r))     # warm
-    rounds, t0 = 0, time.perf_counter()
-    while True:
-        lib.orc_round(h.h, ptr(sizes), n, seed, 1, ptr(mem), None, C.byref(r))
-        rounds += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    assert r.mismatches == 0 and r.nulls == 0
-    return {"value": round(rounds * 2 * n / el / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{rounds} rounds of 2^16 requests (same size distribution, 1 GiB heap, payload in "
-                      f"host memory), one thread, {el:.1f} s"}
+
+class PinnedCore:
+    """Pin this thread to one core (the lowest it may run on) while timing
+    the sequential oracle; the previous affinity comes back on exit."""
+
+    def __enter__(self):
+        self.old = os.sched_getaffinity(0)
+        self.core = min(self.old)
+        os.sched_setaffinity(0, {self.core})
+        return self
+
+    def __exit__(self, *exc):
+        os.sched_setaffinity(0, self.old)
+
+
+class OracleSweep:
+    """The sequential oracle on the headline workload itself: the same 2^20
+    request sizes (same seed) and payload seed as the GPU arm, an 8 GiB heap
+    of 8 KiB chunks, page-array queues, every payload byte written to and
+    read back from host memory (committed lazily: about 1.7 GB is touched)."""
+
+    def __init__(self, threads=THREADS, variant="page_array", seed=SEED):
+        import ctypes as C
+
+        import numpy as np
+
+        import oracle
+        from paper_2504_18211_gb300 import workloads as W
+        self.C, self.n, self.seed = C, threads, seed
+        self.sizes = W.sweep_sizes(threads, seed=replica_seed(0))
+        self.heap = oracle.OracleHeap(HEAP_BYTES, CHUNK, variant)
+        self.mem = np.zeros(HEAP_BYTES, np.uint8)
+        self.want = oracle.expected_checksums(self.sizes, seed, 1)
+        self.r = oracle.RoundResult()
+
+    def round(self) -> None:
+        C, ptr = self.C, (lambda a: a.ctypes.data_as(self.C.c_void_p))
+        self.heap.lib.orc_round(self.heap.h, ptr(self.sizes), self.n, self.seed, 1, ptr(self.mem), None,
+                                C.byref(self.r))
+        res = self.r.as_dict()
+        assert res == dict(self.want, nulls=0, mismatches=0), res
+
+    def describe(self) -> str:
+        return (f"{self.n} requests of 2^k B (k uniform in [4,13], the GPU arm's sizes and seed), 8 GiB heap, "
+                f"8 KiB chunks, page-array; payload written to and read back from host memory")
+
+
+def cpu_oracle_sample(seconds: float, seed: int = SEED):
+    """The sequential oracle on the headline workload (OracleSweep): one
+    untimed round, then whole rounds for about `seconds`, one thread pinned
+    to one core."""
+    sweep = OracleSweep(seed=seed)
+    with PinnedCore() as pin:
+        sweep.round()
+        rounds, t0 = 0, time.perf_counter()
+        while True:
+            sweep.round()
+            rounds += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    return {"value": round(rounds * 2 * sweep.n / el / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rounds} rounds of the headline workload after 1 untimed ({sweep.describe()}), "
+                      f"one thread pinned to core {pin.core}, {el:.1f} s", **host_cpu()}
 
 
 def run_reference(args):
+    """The reference arm: the sequential oracle on the headline workload,
+    `warmup` untimed rounds then `steps` timed rounds, one thread pinned to
+    one core; rank 0 only."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import ctypes as C
-
-    import numpy as np
-
-    import oracle
-    from paper_2504_18211_gb300 import workloads as W
-    n = 1 << 16
-    sizes = W.sweep_sizes(n)
-    h = oracle.OracleHeap(1 << 30, CHUNK, args.variant)
-    mem = np.zeros(1 << 30, np.uint8)
-    r = oracle.RoundResult()
-    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
-    for _ in range(args.warmup):
-        h.lib.orc_round(h.h, ptr(sizes), n, SEED, 1, ptr(mem), None, C.byref(r))
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        h.lib.orc_round(h.h, ptr(sizes), n, SEED, 1, ptr(mem), None, C.byref(r))
-    el = time.perf_counter() - t0
-    value = args.steps * 2 * n / el / 1e6
-    sample = (f"each step: one round of 2^16 requests of the same size distribution (1 GiB heap, "
-              f"payload in host memory), sequential oracle, one thread")
+    sweep = OracleSweep(threads=args.threads, variant=args.variant)
+    with PinnedCore() as pin:
+        for _ in range(args.warmup):
+            sweep.round()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sweep.round()
+        el = time.perf_counter() - t0
+    value = args.steps * 2 * sweep.n / el / 1e6
+    sample = f"each step one round of the headline workload ({sweep.describe()}), one thread pinned to core {pin.core}"
+    cfg = workload_config(args.threads, args.variant, form="sequential oracle", staging=False)
+    cfg["l2"] = "host memory (CPU)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": workload_config(args.threads, args.variant),
-        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": cfg,
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         **host_cpu()},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 # ---------------------------------------------------------------- GPU arm
-def run_batching(args):
-    """256 request batches, threads per batch log-uniform in [2^10, 2^20], sizes
-    uniform in [4, 8192] B, 16 GiB heap: per-launch (4 and 1 launches per
-    batch), CUDA graph and persistent forms, then the autotuner."""
-    import numpy as np
-    import torch
-
-    import oracle
+def _ensure_lib():
     import paper_2504_18211_gb300 as P
-    from paper_2504_18211_gb300 import batching as BT
     from paper_2504_18211_gb300 import build as B
-    from paper_2504_18211_gb300 import workloads as W
     B.build()
     P.load()
-    sizes, offs = W.batching_workload(n_batches=args.batches)
+    return P
+
+
+def measure_batching(variant="page_array", n_batches=256, reps=2, sample_batches=16, tune=False):
+    """Batching: n_batches request batches, threads per batch log-uniform in
+    [2^10, 2^20], sizes uniform in [4, 8192] B, 16 GiB heap of 8 KiB chunks;
+    every form (four launches per batch, one fused launch per batch, a CUDA
+    graph of those, one persistent kernel; the persistent kernel also with
+    staging).  Verified: no null and no mismatch in any batch of any form,
+    every form's per-batch checksums equal, and the oracle's checksums on the
+    `sample_batches` smallest batches (the oracle folds every word; all 256
+    batches would take it minutes)."""
+    import numpy as np
+
+    import oracle
+    from paper_2504_18211_gb300 import batching as BT
+    from paper_2504_18211_gb300 import workloads as W
+    P = _ensure_lib()
+    sizes, offs = W.batching_workload(n_batches=n_batches)
     run = BT.BatchRun(sizes, offs)
     heap_bytes = 16 << 30
-    res = {"workload": f"batching: {args.batches} batches, {sizes.size} requests, sizes U[4,8192] B, 16 GiB heap",
+    res = {"workload": f"batching: {n_batches} batches, {sizes.size} requests (threads per batch log-uniform in "
+                       f"[2^10,2^20]), sizes U[4,8192] B, 16 GiB heap, 8 KiB chunks, {variant}",
            "forms": {}}
-    with P.Heap(heap_bytes, 8192, args.variant) as heap:
-        for form in BT.FORMS:
-            ms = run.time(heap, form, reps=2)
-            res["forms"][form] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
-        got = run.checks()
-        st = heap.stats()
-        run.close()
-    with P.Heap(heap_bytes, 8192, args.variant, staging=True) as heap:
-        ms = run.time(heap, "persistent", reps=2)
-        res["forms"]["persistent_staged"] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
-        got_staged = run.checks()
-        st = heap.stats() if st["error_bits"] == 0 else st
+    checks, errors = {}, 0
+    for staged in (False, True):
+        with P.Heap(heap_bytes, 8192, variant, staging=staged) as heap:
+            for form in (BT.FORMS if not staged else ("persistent",)):
+                ms = run.time(heap, form, reps=reps)
+                key = form + ("_staged" if staged else "")
+                res["forms"][key] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
+                checks[key] = run.checks()
+            errors |= heap.stats()["error_bits"]
+            run.close()
     o = offs.astype(np.int64)
-    want = [oracle.expected_checksums(sizes[o[b]:o[b + 1]], run.seed + b, 1) for b in range(offs.size - 1)]
-    res["verified"] = all(g == dict(w, nulls=0, mismatches=0) and gs == g for g, gs, w in zip(got, got_staged, want)) \
-        and st["error_bits"] == 0
-    sub_sizes, sub_offs = sizes[: int(offs[16])], offs[:17]
-    tune_run = BT.BatchRun(sub_sizes, sub_offs)
-    best, table = BT.autotune(P.Heap, tune_run, heap_bytes)
-    res["autotune"] = {"best": best, "table": table, "trial": "first 16 batches, persistent form"}
-    if best:
-        with P.Heap(heap_bytes, best["chunk"], best["variant"]) as heap:
-            ms = run.time(heap, "persistent", reps=2, blocks_per_sm=best["warps_per_sm"] // 8)
-            res["tuned_persistent"] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
-    print(json.dumps(res))
+    counts = np.diff(o)
+    pick = np.argsort(counts, kind="stable")[:sample_batches]
+    want = {int(b): oracle.expected_checksums(sizes[o[b]:o[b + 1]], run.seed + int(b), 1) for b in pick}
+    first = next(iter(checks.values()))
+    ok = errors == 0 and all(c == first for c in checks.values())
+    ok = ok and all(c["nulls"] == 0 and c["mismatches"] == 0 for c in first)
+    ok = ok and all(first[b] == dict(w, nulls=0, mismatches=0) for b, w in want.items())
+    res["verified"] = bool(ok)
+    res["verified_by"] = (f"every batch of every form: no null, no mismatch, equal checksums across forms; oracle "
+                          f"checksums on the {len(pick)} smallest batches ({int(counts[pick].sum())} requests)")
+    base = res["forms"]["per_launch4"]["ms_per_pass"]
+    res["speedup_vs_per_launch4"] = {k: round(base / v["ms_per_pass"], 2) for k, v in res["forms"].items()}
+    if tune:
+        sub_sizes, sub_offs = sizes[: int(offs[16])], offs[:17]
+        tune_run = BT.BatchRun(sub_sizes, sub_offs)
+        best, table = BT.autotune(P.Heap, tune_run, heap_bytes)
+        res["autotune"] = {"best": best, "table": table, "trial": "first 16 batches, persistent form"}
+        if best:
+            with P.Heap(heap_bytes, best["chunk"], best["variant"]) as heap:
+                ms = run.time(heap, "persistent", reps=reps, blocks_per_sm=best["warps_per_sm"] // 8)
+                res["tuned_persistent"] = {"ms_per_pass": round(ms, 3), "mops": round(2 * run.n / (ms / 1e3) / 1e6, 1)}
+    del run
+    return res
 
 
-def run_serving(args):
-    """64 GiB heap of 16 KiB blocks; Poisson session arrivals (2000/s, 10 ms
-    steps); lognormal session sizes (median 4 MiB, sigma 1); one block per
-    session per step; admission up to 95 % of the blocks; 2000 steps in one
-    cooperative kernel, and as four plain launches per step for comparison."""
+def measure_serving(variants=(("page_array", "persistent"), ("page_array", "per_launch")), steps=2000,
+                    detail=False):
+    """Serving: 64 GiB heap of 16 KiB blocks; Poisson session arrivals
+    (2000/s, 10 ms steps); lognormal session sizes (median 4 MiB, sigma 1);
+    one block per session per step; admission up to 95 % of the blocks;
+    `steps` steps in one cooperative kernel (persistent) or four plain
+    launches per step (per_launch).  Verified against the oracle's admission
+    schedule and per-session checksums (64 sampled completed sessions)."""
     import numpy as np
     import torch
 
     import oracle
-    import paper_2504_18211_gb300 as P
-    from paper_2504_18211_gb300 import build as B
-    from paper_2504_18211_gb300 import workloads as W
     from oracle.patterns import serving_schedule
+    from paper_2504_18211_gb300 import workloads as W
     from paper_2504_18211_gb300.serving import ServeRun
-    B.build()
-    P.load()
-    steps, block, heap_bytes = 2000, 16384, 64 << 30
+    P = _ensure_lib()
+    block, heap_bytes = 16384, 64 << 30
     arrive, blocks = W.serving_workload(steps=steps)
     cap = int(0.95 * heap_bytes // block)
-    res = {"workload": f"serving: {arrive.size} sessions arriving over {steps} steps of 10 ms (2000/s), "
-                       f"lognormal sizes median 4 MiB sigma 1 (<= 64 MiB), 16 KiB blocks, 64 GiB heap, cap 95 %"}
-    for variant, form in ((args.variant, "persistent"), (args.variant, "per_launch"), ("chunk_array", "persistent")):
+    admit, done, _ = serving_schedule(arrive, blocks, steps, 16384, cap)
+    fin = np.flatnonzero(done >= 0)
+    sample = fin[:: max(1, fin.size // 64)]
+    res = {"workload": f"serving: {arrive.size} sessions arriving over {steps} steps of 10 ms (2000/s), lognormal "
+                       f"sizes median 4 MiB sigma 1 (<= 64 MiB), 16 KiB blocks, 64 GiB heap, admission cap 95 %"}
+    for variant, form in variants:
         run = ServeRun(arrive, blocks, n_slots=16384, max_blocks=4096, steps=steps)
         with P.Heap(heap_bytes, block, variant) as heap:
             ms = run.run(heap, cap, form=form)
             r = run.results()
             st = heap.stats()
-        admit, done, _ = serving_schedule(arrive, blocks, steps, 16384, cap)
-        fin = np.flatnonzero(done >= 0)
-        sample = fin[:: max(1, fin.size // 64)]
-        ok = all((int(r["xor"][s]), int(r["sum"][s])) == (
-            lambda e: (e["xor64"], e["sum64"]))(oracle.expected_checksums(
-                np.full(int(blocks[s]), block, np.uint32), (run.seed + int(s)) & 0xFFFFFFFF, 1)) for s in sample)
+        ok = all((int(r["xor"][s]), int(r["sum"][s])) == (lambda e: (e["xor64"], e["sum64"]))(
+            oracle.expected_checksums(np.full(int(blocks[s]), block, np.uint32), (run.seed + int(s)) & 0xFFFFFFFF, 1))
+            for s in sample)
         lat = r["step_us"]
         ops = r["mallocs"] + r["frees"]
-        ph = {k: {"p50": round(float(np.percentile(v, 50)), 1), "p99": round(float(np.percentile(v, 99)), 1),
-                  "max": round(float(v.max()), 1), "total_ms": round(float(v.sum()) / 1e3, 1)}
-              for k, v in r["phases"].items()}
-        slow = np.argsort(lat)[-5:][::-1]
-        res[variant if form == "persistent" else f"{variant}_per_launch"] = {"form": form, "ms": round(ms, 2), "mops": round(ops / (ms / 1e3) / 1e6, 1),
-                        "step_us_p50": round(float(np.percentile(lat, 50)), 1),
-                        "step_us_p99": round(float(np.percentile(lat, 99)), 1),
-                        "phases": ph, "slowest_steps": [int(i) + 1 for i in slow],
-                        "mallocs": r["mallocs"], "frees": r["frees"], "failed": r["failed"],
-                        "admitted": int((r["admit"] >= 0).sum()), "completed": int((r["done"] >= 0).sum()),
-                        "peak_committed_blocks_cap": cap,
-                        "verified": bool(ok and np.array_equal(r["admit"], admit) and np.array_equal(r["done"], done)
-                                         and r["error"] == 0 and st["error_bits"] == 0 and np.all(r["mism"][fin] == 0))}
+        row = {"form": form, "ms": round(ms, 2), "mops": round(ops / (ms / 1e3) / 1e6, 1),
+               "step_us_p50": round(float(np.percentile(lat, 50)), 1),
+               "step_us_p99": round(float(np.percentile(lat, 99)), 1),
+               "mallocs": r["mallocs"], "frees": r["frees"], "failed": r["failed"],
+               "admitted": int((r["admit"] >= 0).sum()), "completed": int((r["done"] >= 0).sum()),
+               "verified": bool(ok and np.array_equal(r["admit"], admit) and np.array_equal(r["done"], done)
+                                and r["error"] == 0 and st["error_bits"] == 0 and np.all(r["mism"][fin] == 0))}
+        if detail:
+            row["phases"] = {k: {"p50": round(float(np.percentile(v, 50)), 1),
+                                 "p99": round(float(np.percentile(v, 99)), 1),
+                                 "max": round(float(v.max()), 1), "total_ms": round(float(v.sum()) / 1e3, 1)}
+                             for k, v in r["phases"].items()}
+            row["slowest_steps"] = [int(i) + 1 for i in np.argsort(lat)[-5:][::-1]]
+            row["peak_committed_blocks_cap"] = cap
+        res[variant if form == "persistent" else f"{variant}_per_launch"] = row
         del run
         torch.cuda.empty_cache()
-    print(json.dumps(res))
+    return res
 
 
-def run_graph(args):
-    """2^20 vertices, 2^24 directed edges with power-law endpoints (degree
-    exponent 2.1), lists from 4 entries growing by malloc 2x / copy / free
-    old, 16 GiB heap of 8 KiB chunks; one insertion kernel timed."""
+def measure_graph(variants=("page_array", "chunk_array")):
+    """Graph growth: 2^20 vertices, 2^24 directed edges with power-law
+    endpoints (degree exponent 2.1), lists from 4 entries growing by malloc
+    2x / copy / free old, 16 GiB heap of 8 KiB chunks; one insertion kernel
+    timed.  Verified: degrees equal the edge list's, per-class malloc / free
+    counts equal the oracle's closed form of the growth rule."""
     import numpy as np
     import torch
 
-    import paper_2504_18211_gb300 as P
-    from paper_2504_18211_gb300 import build as B
-    from paper_2504_18211_gb300 import workloads as W
     from oracle.patterns import graph_class_counts
+    from paper_2504_18211_gb300 import workloads as W
     from paper_2504_18211_gb300.graph import GraphRun
-    B.build()
-    P.load()
+    P = _ensure_lib()
     nv, ne, chunk, heap_bytes = 1 << 20, 1 << 24, 8192, 16 << 30
     src, dst = W.graph_workload(nv, ne)
+    want_deg = np.bincount(src, minlength=nv)
+    m, f, _ = graph_class_counts(want_deg, chunk, 10)
     res = {"workload": "graph growth: 2^20 vertices, 2^24 edges, power-law endpoints (alpha 2.1), "
                        "lists 4 -> doubling -> one chunk -> chained 8 KiB segments, 16 GiB heap"}
-    for variant in (args.variant, "chunk_array"):
+    for variant in variants:
         g = GraphRun(src, dst, nv)
         with P.Heap(heap_bytes, chunk, variant) as heap:
             g.init(heap)
@@ -396,9 +475,8 @@ def run_graph(args):
             ms = a.elapsed_time(b)
             st = heap.stats()
             deg = g.degrees()
-            m, f, _ = graph_class_counts(deg, chunk, heap.n_classes)
             ops = sum(st["mallocs"]) + sum(st["frees"]) - sum(st0["mallocs"])
-            ok = (np.array_equal(deg, np.bincount(src, minlength=nv)) and st["mallocs"] == m.tolist()
+            ok = (np.array_equal(deg, want_deg) and st["mallocs"] == m.tolist()
                   and st["frees"] == f.tolist() and st["error_bits"] == 0 and g.ctl_dict()["failed"] == 0)
             res[variant] = {"ms": round(ms, 2), "appends_per_s": round(ne / (ms / 1e3), 1),
                             "alloc_ops": ops, "alloc_mops": round(ops / (ms / 1e3) / 1e6, 2),
@@ -406,7 +484,20 @@ def run_graph(args):
             g.free(heap)
         del g
         torch.cuda.empty_cache()
-    print(json.dumps(res))
+    return res
+
+
+def run_batching(args):
+    print(json.dumps(measure_batching(args.variant, args.batches, tune=True)))
+
+
+def run_serving(args):
+    print(json.dumps(measure_serving(((args.variant, "persistent"), (args.variant, "per_launch"),
+                                      ("chunk_array", "persistent")), detail=True)))
+
+
+def run_graph(args):
+    print(json.dumps(measure_graph((args.variant, "chunk_array"))))
 
 
 def run_axes(args):
@@ -607,12 +698,35 @@ def main():
 
     if not args.no_extras:
         line.update(extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk))
+        heap.close()
+        torch.cuda.empty_cache()
+        line.update(added_patterns())
         line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
     heap.close()
     print(json.dumps(line))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def added_patterns() -> dict:
+    """The three added usage patterns at their full sizes, each verified:
+    batching (every form; fused / graph / persistent against four launches
+    per batch), serving (one cooperative loop against four launches per
+    step; p50 / p99 step latency) and graph growth."""
+    out = {}
+    bt = measure_batching("page_array")
+    out["batching"] = {"workload": bt["workload"], "mops": {k: v["mops"] for k, v in bt["forms"].items()},
+                       "ms_per_pass": {k: v["ms_per_pass"] for k, v in bt["forms"].items()},
+                       "speedup_vs_per_launch4": bt["speedup_vs_per_launch4"], "verified": bt["verified"],
+                       "verified_by": bt["verified_by"]}
+    sv = measure_serving()
+    loop, pl = sv["page_array"], sv["page_array_per_launch"]
+    out["serving"] = {"workload": sv["workload"], "persistent": loop, "per_launch": pl,
+                      "speedup_vs_per_launch": round(pl["ms"] / loop["ms"], 3),
+                      "verified": loop["verified"] and pl["verified"]}
+    out["graph"] = measure_graph(("page_array",))
+    return out
 
 
 def timed(torch, stream, fn, reps=1, prefill=True):

@@ -316,6 +316,9 @@ ouro_status ouro_batch_graph_destroy(ouro_batch_graph *g);
  *   d_free_stack 2*n_slots slot ids (the free-slot stack, then the step's
  *   list of finished sessions, whose blocks are freed in tasks of 32 dealt
  *   to the warps in turn).
+ * EINVAL unless block_bytes is a non-zero multiple of 16 of at most the
+ * heap's chunk_bytes (the block payload moves whole 16-byte units), and for
+ * a null buffer or n_slots / max_blocks of 0.
  * ENOTSUP if the device cannot launch cooperative kernels.  A grid barrier
  * whose wait runs out sets d_ctl[4] and ends the kernel. */
 ouro_status ouro_serve(ouro_heap *h, const uint32_t *d_arrive_step, const uint32_t *d_blocks, uint32_t n_sessions,

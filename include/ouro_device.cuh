@@ -1657,22 +1657,47 @@ template <int WARPS>
 struct ouro_block_ctx {
   unsigned char cnt[WARPS][OURO_MAX_CLASSES];
   unsigned ids[WARPS][OURO_MAX_CLASSES][OURO_STAGE_CAP];
+  unsigned busy[WARPS];   /* bit c: a lane group of the warp holds class c's stack (public staged calls) */
+  ouro_heap_dev heap;     /* the heap of the staged public calls (ouro_block_begin(ctx, h)) */
 };
 
 namespace ouro {
 namespace detail {
 
-/* staged malloc for page queues; every lane of the warp's call mask calls */
-template <int V, int WARPS>
-__device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, unsigned long long n, bool want) {
-  const unsigned mask = __activemask();
+/* LOCKED: callers whose warps may call in lane subsets that run at the same
+ * time (divergent code in user kernels).  A group leader then takes its
+ * class's stack with a try-lock bit of the warp (ctx.busy) and holds it
+ * until its lanes have read or written their ids; a stack that another
+ * subset holds is skipped (the requests go to the queues). */
+template <bool LOCKED, int WARPS>
+__device__ __forceinline__ bool stack_try_take(ouro_block_ctx<WARPS> &ctx, unsigned w, int cls) {
+  if (!LOCKED) return true;
+  const unsigned bit = 1u << cls;
+  if (atomicOr(&ctx.busy[w], bit) & bit) return false;
+  __threadfence_block();
+  return true;
+}
+template <bool LOCKED, int WARPS>
+__device__ __forceinline__ void stack_release(ouro_block_ctx<WARPS> &ctx, unsigned w, int cls) {
+  if (!LOCKED) return;
+  __threadfence_block();
+  atomicAnd(&ctx.busy[w], ~(1u << cls));
+}
+
+/* staged malloc for page queues; every lane of mask calls (mask: the calling
+ * lanes, or only the calling lane for callers in arbitrary divergent code) */
+template <int V, int WARPS, bool LOCKED = false, int FILL = 1>
+__device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, unsigned long long n, bool want,
+                              unsigned mask) {
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   int cls = want ? size_class(h, n) : -1;
   if (want && cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
   const unsigned g = __match_any_sync(mask, cls);
   const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
   unsigned have = 0, take = 0;
-  if (cls >= 0 && lane == leader) {
+  bool held = false;
+  if (cls >= 0 && cls < (int)h.n_classes && lane == leader && stack_try_take<LOCKED>(ctx, w, cls)) {
+    held = true;
     have = ctx.cnt[w][cls];
     take = min(have, k);
     ctx.cnt[w][cls] = (unsigned char)(have - take);
@@ -1692,18 +1717,23 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
   }
   if (cls >= 0 && lane == leader && take) stat_add(h, cls, OURO_ST_MALLOC, take);
   __syncwarp(mask);
+  if (held) stack_release<LOCKED>(ctx, w, cls);
   const int rest = (cls >= 0 && rank >= take) ? cls : -1;   /* served lanes help the rest */
   if (__any_sync(mask, rest >= 0)) {
-    void *p = page_malloc<V>(h, rest, mask);
+    void *p = page_malloc<V, FILL>(h, rest, mask);
     if (rest >= 0) res = p;
   }
   return res;
 }
-
-/* staged free for page queues; every lane of the warp's call mask calls */
 template <int V, int WARPS>
-__device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
-  const unsigned mask = __activemask();
+__device__ __forceinline__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h,
+                                              unsigned long long n, bool want) {
+  return stage_malloc<V, WARPS>(ctx, h, n, want, __activemask());
+}
+
+/* staged free for page queues; every lane of mask calls (as stage_malloc) */
+template <int V, int WARPS, bool LOCKED = false>
+__device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p, unsigned mask) {
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   unsigned item = 0;
   int cls = -1;
@@ -1726,7 +1756,9 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
   const unsigned g = __match_any_sync(mask, cls);
   const unsigned leader = __ffs(g) - 1, rank = __popc(g & lanemask_lt()), k = __popc(g);
   unsigned have = 0, take = 0;
-  if (cls >= 0 && cls < (int)h.n_classes && lane == leader) {   /* runs are not staged */
+  bool held = false;
+  if (cls >= 0 && cls < (int)h.n_classes && lane == leader && stack_try_take<LOCKED>(ctx, w, cls)) {
+    held = true;                                                /* runs are not staged */
     have = ctx.cnt[w][cls];
     take = min(OURO_STAGE_CAP - have, k);
     ctx.cnt[w][cls] = (unsigned char)(have + take);
@@ -1736,8 +1768,13 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
   take = __shfl_sync(mask, take, leader);
   if (cls >= 0 && rank < take) ctx.ids[w][cls][have + rank] = item;
   __syncwarp(mask);
+  if (held) stack_release<LOCKED>(ctx, w, cls);
   const unsigned rest = __ballot_sync(mask, cls >= 0 && rank >= take);
   if (rest && ((rest >> lane) & 1)) page_free<V>(h, cls, item, rest);
+}
+template <int V, int WARPS>
+__device__ __forceinline__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
+  stage_free<V, WARPS>(ctx, h, p, __activemask());
 }
 
 }  // namespace detail
@@ -1748,6 +1785,7 @@ template <int WARPS>
 __device__ void ouro_block_begin(ouro_block_ctx<WARPS> &ctx) {
   for (unsigned i = threadIdx.x; i < WARPS * OURO_MAX_CLASSES; i += blockDim.x)
     (&ctx.cnt[0][0])[i] = 0;
+  for (unsigned i = threadIdx.x; i < WARPS; i += blockDim.x) ctx.busy[i] = 0;
   __syncthreads();
 }
 
@@ -1778,31 +1816,69 @@ __device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev
 }
 
 /* ------------------------------------------------------------- public API */
-/* Allocate n bytes from the heap; null when n is 0 or above 1 MiB, when
- * the heap is exhausted, or when a bounded wait ran out. */
-static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t n) {
-  using namespace ouro::detail;
-  const unsigned mask = __activemask();
-  const int cls = size_class(h, n);
-  if (cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+/* Two ways to call, both on an ouro_heap_dev passed by value to the kernel:
+ *
+ *   ouro_malloc(h, n) / ouro_free(h, p)
+ *     from anywhere: any lane, in any divergent code, alone or with others.
+ *     Each calling lane runs the queue steps on its own (its warp-level
+ *     steps name only itself), so no assumption is made about which lanes
+ *     of the warp call at the same time.
+ *
+ *   ouro_malloc_warp(h, n, want) / ouro_free_warp(h, p)
+ *     warp-collective: all 32 lanes of the warp call at the same point of the
+ *     program (a lane without a request passes want = false, or p = null).
+ *     Lanes that ask for the same class are served by one queue operation
+ *     (warp aggregation with __match_any_sync), and a carve fills the new
+ *     slots 32 lanes wide.  This is the form the library's own kernels use.
+ *
+ * The lane-private form exists because warp aggregation over the lanes that
+ * __activemask() reports is not safe when several lane subsets of one warp
+ * are inside the allocator at the same time (some lanes freeing while the
+ * others already allocate again): GPU tests of such kernels found queue
+ * slots produced twice, runs handed out twice and blocks overwritten by
+ * another request.  With one lane per call, or the whole warp per call,
+ * the same tests pass. */
+namespace ouro {
+namespace detail {
+/* One queue form each, out of line: the run-time dispatch of the public
+ * calls below picks one of these (and each compiles as its own function).
+ * FILL: slot writes in flight per lane when a carve fills new slots (a lane
+ * on its own fills a carve alone). */
+template <int V, int FILL>
+__device__ __noinline__ void *public_malloc_v(const ouro_heap_dev &h, int cls, unsigned mask) {
+  if constexpr (ouro_page_queues(V)) return page_malloc<V, FILL>(h, cls, mask);   /* pages and runs */
+  else return chunk_or_run_malloc<V>(h, cls, mask);
+}
+
+/* cls, item: from locate (a run already marked free), or -1 */
+template <int V>
+__device__ __noinline__ void public_free_v(const ouro_heap_dev &h, int cls, unsigned item, void *p, unsigned mask) {
+  if constexpr (ouro_page_queues(V)) {
+    const unsigned vmask = __ballot_sync(mask, cls >= 0);
+    if (cls >= 0) page_free<V>(h, cls, item, vmask);
+  } else {
+    chunk_or_run_free<V>(h, cls, item, p, mask);
+  }
+}
+
+template <int FILL>
+__device__ __forceinline__ void *public_malloc(const ouro_heap_dev &h, size_t n, bool want, unsigned mask) {
+  const int cls = want ? size_class(h, n) : -1;
+  if (want && cls < 0) stat_add(h, OURO_ROW_NONE, n == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
   if (!__any_sync(mask, cls >= 0)) return nullptr;
   /* lanes without a class stay in as helpers of the warp's carves */
   switch (h.variant) {
-    case OURO_PAGE_ARRAY: return page_malloc<OURO_PAGE_ARRAY>(h, cls, mask);
-    case OURO_PAGE_VLIST: return page_malloc<OURO_PAGE_VLIST>(h, cls, mask);
-    case OURO_PAGE_VARRAY: return page_malloc<OURO_PAGE_VARRAY>(h, cls, mask);
-    case OURO_CHUNK_ARRAY: return chunk_or_run_malloc<OURO_CHUNK_ARRAY>(h, cls, mask);
-    case OURO_CHUNK_VLIST: return chunk_or_run_malloc<OURO_CHUNK_VLIST>(h, cls, mask);
-    case OURO_CHUNK_VARRAY: return chunk_or_run_malloc<OURO_CHUNK_VARRAY>(h, cls, mask);
+    case OURO_PAGE_ARRAY: return public_malloc_v<OURO_PAGE_ARRAY, FILL>(h, cls, mask);
+    case OURO_PAGE_VLIST: return public_malloc_v<OURO_PAGE_VLIST, FILL>(h, cls, mask);
+    case OURO_PAGE_VARRAY: return public_malloc_v<OURO_PAGE_VARRAY, FILL>(h, cls, mask);
+    case OURO_CHUNK_ARRAY: return public_malloc_v<OURO_CHUNK_ARRAY, FILL>(h, cls, mask);
+    case OURO_CHUNK_VLIST: return public_malloc_v<OURO_CHUNK_VLIST, FILL>(h, cls, mask);
+    case OURO_CHUNK_VARRAY: return public_malloc_v<OURO_CHUNK_VARRAY, FILL>(h, cls, mask);
     default: return nullptr;
   }
 }
 
-/* Return a block to the heap; null is ignored; a pointer that is not a live
- * block start sets OURO_ERR_BAD_FREE (or OURO_ERR_DOUBLE_FREE) and is ignored. */
-static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
-  using namespace ouro::detail;
-  const unsigned mask = __activemask();
+__device__ __forceinline__ void public_free(const ouro_heap_dev &h, void *p, unsigned mask) {
   unsigned item = 0;
   int cls = -1;
   if (p) {
@@ -1819,17 +1895,138 @@ static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
       if (old & bit) { set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_DOUBLE); cls = -1; }
     }
   }
-  if (h.variant == OURO_CHUNK_ARRAY) { chunk_or_run_free<OURO_CHUNK_ARRAY>(h, cls, item, p, mask); return; }
-  if (h.variant == OURO_CHUNK_VLIST) { chunk_or_run_free<OURO_CHUNK_VLIST>(h, cls, item, p, mask); return; }
-  if (h.variant == OURO_CHUNK_VARRAY) { chunk_or_run_free<OURO_CHUNK_VARRAY>(h, cls, item, p, mask); return; }
-  const unsigned vmask = __ballot_sync(mask, cls >= 0);
-  if (cls < 0) return;
   switch (h.variant) {
-    case OURO_PAGE_ARRAY: page_free<OURO_PAGE_ARRAY>(h, cls, item, vmask); break;
-    case OURO_PAGE_VLIST: page_free<OURO_PAGE_VLIST>(h, cls, item, vmask); break;
-    case OURO_PAGE_VARRAY: page_free<OURO_PAGE_VARRAY>(h, cls, item, vmask); break;
+    case OURO_PAGE_ARRAY: public_free_v<OURO_PAGE_ARRAY>(h, cls, item, p, mask); break;
+    case OURO_PAGE_VLIST: public_free_v<OURO_PAGE_VLIST>(h, cls, item, p, mask); break;
+    case OURO_PAGE_VARRAY: public_free_v<OURO_PAGE_VARRAY>(h, cls, item, p, mask); break;
+    case OURO_CHUNK_ARRAY: public_free_v<OURO_CHUNK_ARRAY>(h, cls, item, p, mask); break;
+    case OURO_CHUNK_VLIST: public_free_v<OURO_CHUNK_VLIST>(h, cls, item, p, mask); break;
+    case OURO_CHUNK_VARRAY: public_free_v<OURO_CHUNK_VARRAY>(h, cls, item, p, mask); break;
     default: break;
   }
+}
+}  // namespace detail
+}  // namespace ouro
+
+/* Allocate n bytes from the heap; null when n is 0 or above 1 MiB, when
+ * the heap is exhausted, or when a bounded wait ran out.  Any lane, any
+ * divergent code. */
+static __device__ __noinline__ void *ouro_malloc(const ouro_heap_dev &h, size_t n) {
+  return ouro::detail::public_malloc<8>(h, n, true, 1u << ouro::detail::laneid());
+}
+
+/* Return a block to the heap; null is ignored; a pointer that is not a live
+ * block start sets OURO_ERR_BAD_FREE (or OURO_ERR_DOUBLE_FREE) and is
+ * ignored.  Any lane, any divergent code. */
+static __device__ __noinline__ void ouro_free(const ouro_heap_dev &h, void *p) {
+  ouro::detail::public_free(h, p, 1u << ouro::detail::laneid());
+}
+
+/* Warp-collective malloc: every lane of the warp calls at the same point;
+ * want = false: the lane asks for nothing (and returns null).  Same answers
+ * as ouro_malloc, with one queue operation per class among the lanes. */
+static __device__ __noinline__ void *ouro_malloc_warp(const ouro_heap_dev &h, size_t n, bool want) {
+  __syncwarp();
+  return ouro::detail::public_malloc<1>(h, n, want, 0xffffffffu);
+}
+
+/* Warp-collective free: every lane of the warp calls at the same point
+ * (p = null for a lane with nothing to free). */
+static __device__ __noinline__ void ouro_free_warp(const ouro_heap_dev &h, void *p) {
+  __syncwarp();
+  ouro::detail::public_free(h, p, 0xffffffffu);
+}
+
+/* ------------------------------------------------- public API, staged form */
+/* Block staging for user kernels: the heap is named once per block.
+ *
+ *   __shared__ ouro_block_ctx<8> ctx;      // WARPS >= warps of the block
+ *   ouro_block_begin(ctx, h);              // every thread of the block
+ *   void *p = ouro_malloc(ctx, n);         // any lane, divergent code
+ *   ouro_free(ctx, p);
+ *   void *q = ouro_malloc_warp(ctx, n, want);   // or warp-collective
+ *   ouro_free_warp(ctx, q);
+ *   ouro_block_end(ctx);                   // every thread, before the kernel exits
+ *
+ * On page queues a freed page stays on its warp's shared-memory stack (up to
+ * OURO_STAGE_CAP per class) and serves that warp's next malloc of the class
+ * without a queue operation; ouro_block_end returns what is left to the class
+ * queues.  A lane-private call takes the warp's class stack with a try-lock
+ * bit (another lane holding it sends the request to the queues).  On chunk
+ * queues the staged calls are the plain ones.  The block is one-dimensional
+ * with at most 32 * WARPS threads; a page freed through the staged form
+ * must not be used by another block before ouro_block_end. */
+template <int WARPS>
+__device__ void ouro_block_begin(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h) {
+  if (threadIdx.x == 0) ctx.heap = h;
+  ouro_block_begin(ctx);
+}
+
+template <int WARPS>
+__device__ void ouro_block_end(ouro_block_ctx<WARPS> &ctx) {
+  switch (ctx.heap.variant) {
+    case OURO_PAGE_ARRAY: ouro_block_end_v<OURO_PAGE_ARRAY, WARPS>(ctx, ctx.heap); break;
+    case OURO_PAGE_VLIST: ouro_block_end_v<OURO_PAGE_VLIST, WARPS>(ctx, ctx.heap); break;
+    case OURO_PAGE_VARRAY: ouro_block_end_v<OURO_PAGE_VARRAY, WARPS>(ctx, ctx.heap); break;
+    default: __syncthreads(); break;   /* chunk queues stage nothing */
+  }
+}
+
+namespace ouro {
+namespace detail {
+template <int V, int WARPS, int FILL>
+__device__ __noinline__ void *public_stage_malloc_v(ouro_block_ctx<WARPS> &ctx, size_t n, bool want, unsigned mask) {
+  return stage_malloc<V, WARPS, true, FILL>(ctx, ctx.heap, n, want, mask);
+}
+template <int V, int WARPS>
+__device__ __noinline__ void public_stage_free_v(ouro_block_ctx<WARPS> &ctx, void *p, unsigned mask) {
+  stage_free<V, WARPS, true>(ctx, ctx.heap, p, mask);
+}
+template <int WARPS, int FILL>
+__device__ __forceinline__ void *public_stage_malloc(ouro_block_ctx<WARPS> &ctx, size_t n, bool want, unsigned mask) {
+  switch (ctx.heap.variant) {
+    case OURO_PAGE_ARRAY: return public_stage_malloc_v<OURO_PAGE_ARRAY, WARPS, FILL>(ctx, n, want, mask);
+    case OURO_PAGE_VLIST: return public_stage_malloc_v<OURO_PAGE_VLIST, WARPS, FILL>(ctx, n, want, mask);
+    case OURO_PAGE_VARRAY: return public_stage_malloc_v<OURO_PAGE_VARRAY, WARPS, FILL>(ctx, n, want, mask);
+    default: return public_malloc<FILL>(ctx.heap, n, want, mask);
+  }
+}
+template <int WARPS>
+__device__ __forceinline__ void public_stage_free(ouro_block_ctx<WARPS> &ctx, void *p, unsigned mask) {
+  switch (ctx.heap.variant) {
+    case OURO_PAGE_ARRAY: public_stage_free_v<OURO_PAGE_ARRAY, WARPS>(ctx, p, mask); break;
+    case OURO_PAGE_VLIST: public_stage_free_v<OURO_PAGE_VLIST, WARPS>(ctx, p, mask); break;
+    case OURO_PAGE_VARRAY: public_stage_free_v<OURO_PAGE_VARRAY, WARPS>(ctx, p, mask); break;
+    default: public_free(ctx.heap, p, mask); break;
+  }
+}
+}  // namespace detail
+}  // namespace ouro
+
+/* staged malloc, any lane, any divergent code */
+template <int WARPS>
+__device__ void *ouro_malloc(ouro_block_ctx<WARPS> &ctx, size_t n) {
+  return ouro::detail::public_stage_malloc<WARPS, 8>(ctx, n, true, 1u << ouro::detail::laneid());
+}
+
+/* staged free, any lane, any divergent code */
+template <int WARPS>
+__device__ void ouro_free(ouro_block_ctx<WARPS> &ctx, void *p) {
+  ouro::detail::public_stage_free<WARPS>(ctx, p, 1u << ouro::detail::laneid());
+}
+
+/* staged malloc, warp-collective (every lane of the warp calls) */
+template <int WARPS>
+__device__ void *ouro_malloc_warp(ouro_block_ctx<WARPS> &ctx, size_t n, bool want) {
+  __syncwarp();
+  return ouro::detail::public_stage_malloc<WARPS, 1>(ctx, n, want, 0xffffffffu);
+}
+
+/* staged free, warp-collective (every lane of the warp calls) */
+template <int WARPS>
+__device__ void ouro_free_warp(ouro_block_ctx<WARPS> &ctx, void *p) {
+  __syncwarp();
+  ouro::detail::public_stage_free<WARPS>(ctx, p, 0xffffffffu);
 }
 
 #endif

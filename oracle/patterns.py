@@ -32,7 +32,9 @@ def serving_schedule(arrive: np.ndarray, blocks: np.ndarray, steps: int, n_slots
     the first session that does not fit stops admission for the step (no
     overtaking).  Then every active session grows by one block; a session
     that reaches its size completes in that step, frees its blocks and its
-    slot, which count from the next step on.
+    slot, which count from the next step on.  Since an active session grows
+    one block in every step, a session of b blocks admitted at step a
+    completes at step a + b - 1.
 
     Returns (admit step, completion step, blocks grown) per session; -1 for
     a session never admitted / never completed."""
@@ -40,27 +42,26 @@ def serving_schedule(arrive: np.ndarray, blocks: np.ndarray, steps: int, n_slots
     admit = np.full(n, -1, np.int64)
     done = np.full(n, -1, np.int64)
     grown = np.zeros(n, np.int64)
-    active = []
+    completing = {}          # step -> sessions that complete in it
+    active = 0
     nxt = 0
     committed = 0
     for step in range(steps):
         while nxt < n:
             need = int(blocks[nxt])
-            if int(arrive[nxt]) > step or committed + need > cap_blocks or len(active) >= n_slots:
+            if int(arrive[nxt]) > step or committed + need > cap_blocks or active >= n_slots:
                 break
             admit[nxt] = step
             committed += need
-            active.append(nxt)
+            active += 1
+            completing.setdefault(step + need - 1, []).append(nxt)
             nxt += 1
-        still = []
-        for s in active:
-            grown[s] += 1
-            if grown[s] >= int(blocks[s]):
-                done[s] = step
-                committed -= int(blocks[s])
-            else:
-                still.append(s)
-        active = still
+        for s in completing.pop(step, []):
+            done[s] = step
+            committed -= int(blocks[s])
+            active -= 1
+    on = admit >= 0
+    grown[on] = np.minimum(blocks[on].astype(np.int64), steps - admit[on])
     return admit, done, grown
 
 

@@ -79,3 +79,21 @@ def graph_workload(n_vertices: int = 1 << 20, n_edges: int = 1 << 24, alpha: flo
     src = perm[np.minimum(np.searchsorted(cdf, r.random(n_edges), side="right"), n_vertices - 1)]
     dst = perm[np.minimum(np.searchsorted(cdf, r.random(n_edges), side="right"), n_vertices - 1)]
     return src.astype(np.uint32), dst.astype(np.uint32)
+
+
+def mixed_sizes(threads: int, seed: int, chunk_bytes: int = 8192) -> np.ndarray:
+    """Requests of every kind a kernel may make: powers of two 16 B .. one
+    chunk (most), any byte count up to one chunk (30 %: sizes that are not a
+    multiple of 4 included), runs of chunks up to 64 KiB (2 %), 0 bytes (2 %)
+    and above 1 MiB (2 %, answered with null)."""
+    r = rng(seed)
+    kmax = int(chunk_bytes).bit_length() - 1
+    s = (np.int64(1) << r.integers(4, kmax + 1, size=threads)).astype(np.int64)
+    pick = r.random(threads)
+    odd = pick < 0.30
+    s[odd] = r.integers(1, chunk_bytes + 1, size=int(odd.sum()))
+    run = (pick >= 0.30) & (pick < 0.32)
+    s[run] = r.integers(chunk_bytes + 1, 65536 + 1, size=int(run.sum()))
+    s[(pick >= 0.32) & (pick < 0.34)] = 0
+    s[(pick >= 0.34) & (pick < 0.36)] = 2 << 20
+    return s.astype(np.uint32)

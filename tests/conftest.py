@@ -14,3 +14,12 @@ if TESTS not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def pytest_collection_finish(session):
+    """GPU tests of the public device API need the test-only user-kernel
+    library: start its build now, so that it overlaps the other tests."""
+    if any("test_gpu_user_api" in item.nodeid and item.get_closest_marker("gpu") for item in session.items):
+        sys.path.insert(0, os.path.join(TESTS, "cuda"))
+        import build_user
+        build_user.start_background()

@@ -24,7 +24,8 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray"])
+@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray", "chunk_vlist",
+                                     "chunk_varray"])
 def test_graph_growth_matches_edge_list_and_closed_form(P, variant):
     from paper_2504_18211_gb300.graph import GraphRun
     torch = torch_cuda()

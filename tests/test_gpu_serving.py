@@ -30,7 +30,8 @@ def session_checksum(seed, s, nblocks, block_bytes):
     return r["xor64"], r["sum64"]
 
 
-@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray"])
+@pytest.mark.parametrize("variant", ["page_array", "chunk_array", "page_vlist", "page_varray", "chunk_vlist",
+                                     "chunk_varray"])
 def test_serving_loop_matches_model_and_oracle(P, variant):
     from paper_2504_18211_gb300.serving import ServeRun
     torch_cuda()

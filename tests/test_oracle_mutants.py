@@ -110,10 +110,14 @@ def test_mutant_is_caught(name):
 PY_MUTANTS = {
     "admit_overtakes": ("                break\n            admit[nxt] = step",
                         "                nxt += 1\n                continue\n            admit[nxt] = step", "pin_serving_schedule"),
-    "admit_ignores_slots": (" or len(active) >= n_slots:", ":", "pin_serving_schedule"),
+    "admit_ignores_slots": (" or active >= n_slots:", ":", "pin_serving_schedule"),
     "admit_cap_strict": ("committed + need > cap_blocks", "committed + need >= cap_blocks", "pin_serving_schedule"),
-    "complete_one_late": ("if grown[s] >= int(blocks[s]):", "if grown[s] > int(blocks[s]):", "pin_serving_schedule"),
-    "complete_keeps_blocks": ("                committed -= int(blocks[s])\n", "", "pin_serving_schedule"),
+    "complete_one_late": ("completing.setdefault(step + need - 1, [])", "completing.setdefault(step + need, [])",
+                          "pin_serving_schedule"),
+    "complete_keeps_blocks": ("            committed -= int(blocks[s])\n", "", "pin_serving_schedule"),
+    "complete_keeps_slot": ("            active -= 1\n", "", "pin_serving_schedule"),
+    "grown_past_size": ("np.minimum(blocks[on].astype(np.int64), steps - admit[on])", "steps - admit[on]",
+                        "pin_serving_schedule"),
     "growth_stops_early": ("while cap < min(d, max_plain):", "while cap < min(d, max_plain // 2):", "pin_graph_counts"),
     "growth_frees_new_class": ("frees[_class_of_entries(cap)] += 1\n            cap *= 2",
                                "cap *= 2\n            frees[_class_of_entries(cap)] += 1", "pin_graph_counts"),

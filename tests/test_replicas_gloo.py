@@ -91,3 +91,8 @@ def test_reference_arm_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # the line states what ran: the headline workload itself, on a stated host
+    cfg, cb = line["config"], line["cpu_baseline"]
+    assert cfg["threads"] == 1 << 20 and cfg["heap_bytes"] == 8 << 30 and cfg["chunk_bytes"] == 8192
+    assert cb["host_cpus"] == os.cpu_count() and cb["cpu_model"] and cb["cores"] == 1
+    assert "1048576 requests" in cb["sample"] and "pinned to core" in cb["sample"]
