@@ -789,7 +789,9 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
                         "alloc_free_mops": round(2 * n / (af / 1e3) / 1e6, 1),
                         "round_mops": round(2 * n / (round_ms / 1e3) / 1e6, 1)}
 
-    # ---- the other page-queue variant
+    # ---- the other five queue forms, fused (unstaged and staged) and per launch
+    import oracle
+    want_chk = dict(oracle.expected_checksums(sizes_np, SEED, 1), nulls=0, mismatches=0)
     others = {}
     for v in ("page_array", "page_vlist", "chunk_array", "chunk_vlist", "page_varray", "chunk_varray"):
         if v == args.variant:
@@ -800,10 +802,16 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
                 h2.round_fused(sizes, SEED, 1, out=o2)
             fms = timed(torch, stream, lambda: h2.round_fused(sizes, SEED, 1, out=o2), 5)
             pl2 = per_launch(h2, 4)
-            ok = P.check_to_dict(o2)["mismatches"] == 0 and h2.stats()["error_bits"] == 0
-            others[v] = {"fused_mops": round(2 * n / (fms / 1e3) / 1e6, 1),
-                         "alloc_free_mops": round(2 * n / ((pl2["malloc"] + pl2["free"]) / 1e3) / 1e6, 1),
-                         "per_launch_ms": {k: round(x, 4) for k, x in pl2.items()}, "verified": ok}
+            ok = P.check_to_dict(o2) == want_chk and h2.stats()["error_bits"] == 0
+        with P.Heap(HEAP_BYTES, CHUNK, v, staging=True) as h2s:
+            for _ in range(3):
+                h2s.round_fused(sizes, SEED, 1, out=o2)
+            sms2 = timed(torch, stream, lambda: h2s.round_fused(sizes, SEED, 1, out=o2), 5)
+            ok = ok and P.check_to_dict(o2) == want_chk and h2s.stats()["error_bits"] == 0
+        others[v] = {"fused_mops": round(2 * n / (fms / 1e3) / 1e6, 1),
+                     "fused_staged_mops": round(2 * n / (sms2 / 1e3) / 1e6, 1),
+                     "alloc_free_mops": round(2 * n / ((pl2["malloc"] + pl2["free"]) / 1e3) / 1e6, 1),
+                     "per_launch_ms": {k: round(x, 4) for k, x in pl2.items()}, "verified": ok}
     ex["variants"] = others
 
     # ---- the deoptimised form of Sec. 2: no warp aggregation, fences for sleeps

@@ -86,8 +86,8 @@ typedef struct {
   uint32_t max_carve;             /* chunks one carve may take at once (default 65536) */
   uint64_t array_queue_capacity;  /* page-array item limit per class (default 1<<23) */
   uint32_t checked;               /* page queues: track live pages to detect double frees */
-  uint32_t staging;               /* page queues: the library's fused / persistent kernels stage
-                                     freed pages per warp in shared memory (ouro_block_ctx) */
+  uint32_t staging;               /* the library's fused / persistent kernels stage freed pages per
+                                     warp in shared memory (ouro_block_ctx), every queue form */
   uint32_t deopt;                 /* the "deoptimised" form of Sec. 2: no warp aggregation (every
                                      request takes its own queue atomics) and a memory fence where
                                      a waiting thread would __nanosleep; for comparison only */

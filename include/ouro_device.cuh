@@ -1217,6 +1217,28 @@ __device__ inline void chunk_push(const ouro_heap_dev &h, int c, unsigned x) {
   push_one<QF>(h, c, x);
 }
 
+/* Queue item x in class c's queue for every lane of mask with `want` (any
+ * mix of classes): one tail atomic per class group of the warp, then every
+ * such lane publishes its own slot.  Every lane of mask calls. */
+template <int QF>
+__device__ inline void push_group(const ouro_heap_dev &h, int c, unsigned x, bool want, unsigned mask) {
+  constexpr bool VL = QF != OURO_QF_RING;
+  const unsigned pm = __ballot_sync(mask, want);
+  if (!pm) return;
+  const unsigned g = warp_group(h, mask, want ? c : -1) & pm;
+  const unsigned leader = want ? (unsigned)(__ffs(g) - 1) : laneid();
+  unsigned long long t = 0;
+  if (want && laneid() == leader) t = atomicAdd(&qh(h, c)->tail.v, (unsigned long long)__popc(g));
+  t = __shfl_sync(mask, t, leader);
+  if (!want) return;
+  t += __popc(g & lanemask_lt());
+  unsigned long long *cell = slot_at<QF>(h, c, t, true);
+  if (!cell) return;                            /* queue storage exhausted (recorded) */
+  const int rc = put_at(h, cell, t, x, false, VL);
+  if (VL) seg_event<QF>(h, c, cell, 1);
+  if (rc == 1) push_one<QF>(h, c, x);            /* the consumer gave the position up */
+}
+
 /* Called by every lane of vmask; lane `owner` holds the carve lock of class c. */
 template <int V>
 __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
@@ -1338,10 +1360,15 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
     /* the count stays <= 0 until now (frees of reserved pages only return
      * what was reserved), so adding the pages here lifts it above zero
      * exactly once: the chunk is queued once iff it has a free page */
-    for (unsigned k = rk; k < g; k += nl) {
-      const unsigned x = range_chunk(h, cr, k);
-      const int b = atomicAdd(&h.chunk_free[x], (int)ppc);
-      if (b <= 0 && b + (int)ppc >= 1) chunk_push<QF>(h, c, x);
+    for (unsigned k0 = 0; k0 < g; k0 += nl) {
+      const unsigned k = k0 + rk;
+      const unsigned x = k < g ? range_chunk(h, cr, k) : 0;
+      bool lift = false;
+      if (k < g) {
+        const int b = atomicAdd(&h.chunk_free[x], (int)ppc);
+        lift = b <= 0 && b + (int)ppc >= 1;
+      }
+      push_group<QF>(h, c, x, lift, vmask);
     }
     __syncwarp(vmask);
     if (g < m) {
@@ -1610,14 +1637,203 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
   }
   /* 2. count the pages back per chunk; lifting the count from <= 0 queues it */
   const unsigned cg = warp_group(h, mask, cls >= 0 ? x : OURO_NIL) & __ballot_sync(mask, cls >= 0);
+  bool lift = false;
   if (cls >= 0 && lane == (unsigned)(__ffs(cg) - 1)) {
     const int k = __popc(cg);
     __threadfence();
     const int b = atomicAdd(&h.chunk_free[x], k);
-    if (b <= 0 && b + k >= 1) chunk_push<QF>(h, cls, x);
+    lift = b <= 0 && b + k >= 1;
   }
+  push_group<QF>(h, cls, x, lift, mask);   /* the lifted chunks, one tail atomic per class */
   const unsigned sg = warp_group(h, mask, cls);
   if (cls >= 0 && lane == (unsigned)(__ffs(sg) - 1)) stat_add(h, cls, OURO_ST_FREE, __popc(sg));
+}
+
+/* One lane claims `want` free pages of chunk x (its reservation on the
+ * chunk's count guarantees them) from the chunk's bitmap, starting at a
+ * spread word, and writes their page ids (x << ppc_log | page) to dst; a
+ * wait that runs out fills the rest with OURO_NIL and records a timeout. */
+__device__ inline void claim_into(const ouro_heap_dev &h, unsigned x, unsigned ppc_log, unsigned want, unsigned *dst,
+                                  unsigned seed) {
+  const unsigned words_c = ((1u << ppc_log) + 31) >> 5;
+  unsigned *bw = h.bits + (size_t)x * h.words_per_chunk;
+  unsigned w = words_c > 1 ? seed % words_c : 0;
+  unsigned done = 0, empty = 0, ns = h.backoff_min_ns;
+  unsigned v = *(volatile unsigned *)&bw[w];
+  for (unsigned it = 0; done < want && it < h.spin_limit; ++it) {
+    if (v) {
+      unsigned m = 0, tmp = v;
+      for (unsigned k = done; k < want && tmp; ++k) {
+        const unsigned b = tmp & (0u - tmp);
+        m |= b;
+        tmp ^= b;
+      }
+      const unsigned old = atomicAnd(&bw[w], ~m);
+      unsigned cl = old & m;
+      while (cl) {
+        dst[done++] = (x << ppc_log) | (w * 32 + __ffs(cl) - 1);
+        cl &= cl - 1;
+      }
+      v = old & ~m;
+      empty = 0;
+    }
+    if (!v && done < want) {
+      w = (w + 1 == words_c) ? 0 : w + 1;
+      if (++empty > words_c) {          /* a whole pass found nothing: bits still being freed */
+        backoff_wait(h, ns);
+        ns = min(ns * 2, h.backoff_max_ns);
+        empty = 0;
+      }
+      v = *(volatile unsigned *)&bw[w];
+    }
+  }
+  if (done < want) {
+    set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_CLAIM);
+    for (; done < want; ++done) dst[done] = OURO_NIL;
+  }
+}
+
+/* The whole warp (all 32 lanes call) obtains up to `need` pages of class c
+ * from a chunk queue for its block, and writes their page ids to out[0, got).
+ * Each round pops m positions at once -- the chunks the rest needs at one
+ * full chunk each (32 pages each while the queue looks empty), at most 32
+ * -- one per lane: a lane reserves its share on
+ * its chunk's count (or takes its part of a carve's reservation), the
+ * chunks that keep free pages are queued again with one tail atomic, and
+ * every lane claims its pages from its chunk's bitmap.  A position in debt
+ * posts its share (at most 32 pages) for the carve, as chunk_malloc does.
+ * Returns got: fewer than need only when the heap is exhausted (a round
+ * of null answers only ends the acquisition) or a bounded wait ran out. */
+template <int V>
+__device__ unsigned chunk_acquire(const ouro_heap_dev &h, int c, unsigned need, unsigned *out) {
+  constexpr int QF = ouro_qform(V);
+  constexpr bool VL = QF != OURO_QF_RING;
+  constexpr unsigned FULL = 0xffffffffu;
+  ouro_qhdr *q = qh(h, c);
+  const unsigned lane = laneid();
+  const unsigned ppc_log = h.log2_chunk - 4 - c, ppc = 1u << ppc_log;
+  unsigned got = 0;
+  for (unsigned round = 0; got < need && round < h.spin_limit; ++round) {
+    const unsigned rem = need - got;
+    /* share per position: a whole chunk while the queue holds chunks; 32
+     * pages (what a carve reserves for one position) when it looks empty,
+     * so that a carve packs the block's need as the per-warp path does */
+    unsigned gran_log = ppc_log;
+    if (lane == 0 && ld_rlx(&q->tail.v) <= ld_rlx(&q->head.v)) gran_log = min(ppc_log, 5u);
+    gran_log = __shfl_sync(FULL, gran_log, 0);
+    const unsigned gran = 1u << gran_log;
+    const unsigned m = min(32u, (rem + gran - 1) >> gran_log);
+    unsigned long long p0 = 0;
+    if (lane == 0) p0 = atomicAdd(&q->head.v, (unsigned long long)m);
+    p0 = __shfl_sync(FULL, p0, 0);
+    const bool mine = lane < m;
+    const unsigned share = mine ? min(gran, rem - lane * gran) : 0;
+    const unsigned long long pos = p0 + lane;
+    int st = mine ? 0 : 3;              /* 0 waiting, 1 item, 2 null answer, 3 no position */
+    unsigned item = 0;
+    bool posted = false;
+    unsigned long long *cell = nullptr;
+    unsigned ns = h.backoff_min_ns;
+    for (unsigned it = 0;; ++it) {
+      bool debt = false, progressed = false;
+      if (st == 0) {
+        if (!cell) cell = slot_at<QF>(h, c, pos, false);
+        if (cell) {
+          st = try_take<VL>(h, c, cell, pos, &item);
+          if (st) {
+            progressed = true;
+            if (VL) seg_event<QF>(h, c, cell, 1);
+          }
+        }
+        if (!st && pos >= ld_acq(&q->tail.v)) {
+          debt = true;
+          if (!posted) {
+            if (!cell && VL) cell = slot_at<QF>(h, c, pos, true);
+            if (cell) {
+              const unsigned long long e = ld_acq(cell);
+              const int d = slot_d(e, pos);
+              posted = true;
+              if (d == 0 || (VL && d < 0)) cas_ar(cell, e, slot(pos, min(share, 32u)));
+            }
+          }
+        }
+      }
+      const unsigned dmask = __ballot_sync(FULL, debt);
+      if (dmask) {   /* one lock taker: its whole warp carves */
+        const bool lk = lane == (unsigned)(__ffs(dmask) - 1) && try_lock(&q->lock.v);
+        const unsigned lockers = __ballot_sync(FULL, lk);
+        if (lockers) chunk_carve<V>(h, c, FULL, __ffs(lockers) - 1);
+      }
+      if (!__ballot_sync(FULL, st == 0)) break;
+      if (it >= h.spin_limit) {          /* the bounded wait ran out: give the position up */
+        if (st == 0) {
+          if (!cell) cell = slot_at<QF>(h, c, pos, true);
+          unsigned item2 = 0;
+          const int g = cell ? give_up<VL>(h, c, cell, pos, &item2) : 0;
+          if (g == 1 || g == 2) {
+            st = g;
+            item = item2;
+          } else {
+            st = 2;
+            set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_CHUNK_GIVEUP);
+            stat_add(h, c, OURO_ST_CANCEL, 1);
+          }
+          if (VL && cell && g) seg_event<QF>(h, c, cell, 1);
+        }
+        break;
+      }
+      if (!__any_sync(FULL, progressed)) {
+        backoff_wait(h, ns);
+        ns = min(ns * 2, h.backoff_max_ns);
+      } else {
+        ns = h.backoff_min_ns;
+      }
+    }
+    /* reserve the shares on the chunks; chunks that keep free pages go back */
+    unsigned granted = 0, x = 0;
+    bool push = false;
+    if (st == 1) {
+      x = OURO_CQ_ID(item);
+      if (item & OURO_CQ_RES) {
+        const unsigned cnt = OURO_CQ_CNT(item);
+        granted = min(cnt, share);
+        if (cnt > share) {   /* reserved for more than this share: hand back the rest */
+          const int ex = (int)(cnt - share);
+          const int b = atomicAdd(&h.chunk_free[x], ex);
+          push = b <= 0 && b + ex >= 1;
+        }
+      } else {
+        const int old = atomicSub(&h.chunk_free[x], (int)share);
+        granted = old <= 0 ? 0 : min((unsigned)old, share);
+        if (old - (int)share >= 1) {
+          push = true;
+        } else if (granted < share) {
+          const int ex = (int)(share - granted);
+          const int b = atomicAdd(&h.chunk_free[x], ex);
+          push = b <= 0 && b + ex >= 1;
+        }
+      }
+    }
+    push_group<QF>(h, c, x, push, FULL);
+    /* every lane claims its pages into its part of out */
+    unsigned off = granted;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(FULL, off, o);
+      if ((int)lane >= o) off += y;
+    }
+    const unsigned total = __shfl_sync(FULL, off, 31);
+    off -= granted;
+    if (granted)
+      claim_into(h, x, ppc_log, granted, out + got + off,
+                 (((blockIdx.x * blockDim.x + threadIdx.x) * 0x9E3779B1u) ^ (x * 0x85EBCA6Bu) ^ round) >> 7);
+    got += total;
+    /* a round whose every position was answered null finds the heap
+     * exhausted: the rest of the need is answered null (a round with some
+     * chunks goes on, so pages queued meanwhile are still handed out) */
+    if (!__any_sync(FULL, st == 1)) break;
+  }
+  __syncwarp();
+  return got;
 }
 
 /* Chunk-queue heaps: classes within a chunk go to the chunk queues, runs
@@ -1643,15 +1859,17 @@ __device__ void chunk_or_run_free(const ouro_heap_dev &h, int cls, unsigned item
 }  // namespace detail
 }  // namespace ouro
 
-/* ------------------------------------------------- block staging (page queues) */
+/* ------------------------------------------------------------ block staging */
 /* Shared-memory staging of freed pages: every warp of a block owns, per size
  * class, a stack of up to OURO_STAGE_CAP page ids.  A staged free pushes the
  * page id there instead of into the class queue; a later staged malloc of
  * the same class in the same warp pops it, with no global atomic and no
  * queue slot traffic.  Stacks are warp-private, so no synchronisation beyond
  * __syncwarp is needed.  ouro_block_end pushes what is left back to the
- * class queues; a kernel must call it before it exits.  Page queues only:
- * with chunk queues the staged calls go straight to the heap. */
+ * class queues (page queues) or to their chunks (chunk queues); a kernel must
+ * call it before it exits.  Runs above one chunk are not staged.  On chunk
+ * queues a staged page keeps its bitmap bit clear (it is still taken from
+ * its chunk's point of view) until the flush. */
 #define OURO_STAGE_CAP 16
 template <int WARPS>
 struct ouro_block_ctx {
@@ -1684,7 +1902,7 @@ __device__ __forceinline__ void stack_release(ouro_block_ctx<WARPS> &ctx, unsign
   atomicAnd(&ctx.busy[w], ~(1u << cls));
 }
 
-/* staged malloc for page queues; every lane of mask calls (mask: the calling
+/* staged malloc; every lane of mask calls (mask: the calling
  * lanes, or only the calling lane for callers in arbitrary divergent code) */
 template <int V, int WARPS, bool LOCKED = false, int FILL = 1>
 __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, unsigned long long n, bool want,
@@ -1707,7 +1925,7 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
   void *res = nullptr;
   if (cls >= 0 && rank < take) {
     const unsigned item = ctx.ids[w][cls][have - 1 - rank];
-    if (h.checked) {
+    if (ouro_page_queues(V) && h.checked) {
       const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
       const unsigned bit = 1u << (pg & 31);
       const unsigned old = atomicAnd(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], ~bit);
@@ -1720,7 +1938,9 @@ __device__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h
   if (held) stack_release<LOCKED>(ctx, w, cls);
   const int rest = (cls >= 0 && rank >= take) ? cls : -1;   /* served lanes help the rest */
   if (__any_sync(mask, rest >= 0)) {
-    void *p = page_malloc<V, FILL>(h, rest, mask);
+    void *p;
+    if constexpr (ouro_page_queues(V)) p = page_malloc<V, FILL>(h, rest, mask);
+    else p = chunk_or_run_malloc<V>(h, rest, mask);
     if (rest >= 0) res = p;
   }
   return res;
@@ -1731,7 +1951,7 @@ __device__ __forceinline__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const 
   return stage_malloc<V, WARPS>(ctx, h, n, want, __activemask());
 }
 
-/* staged free for page queues; every lane of mask calls (as stage_malloc) */
+/* staged free; every lane of mask calls (as stage_malloc) */
 template <int V, int WARPS, bool LOCKED = false>
 __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p, unsigned mask) {
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
@@ -1742,13 +1962,21 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (cls >= (int)h.n_classes) {
       if (!run_mark_free(h, cls, item)) cls = -1;
-    } else if (h.checked) {
+    } else if (ouro_page_queues(V) && h.checked) {
       const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
       const unsigned bit = 1u << (pg & 31);
       __threadfence();
       const unsigned old = atomicOr(&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)], bit);
       if (old & bit) {
         set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_PAGE_DOUBLE);
+        cls = -1;
+      }
+    } else if (!ouro_page_queues(V)) {
+      /* chunk queues: a page back in its chunk has its bit set; a staged
+       * page keeps it clear until the block flushes it */
+      const unsigned sh = h.log2_chunk - 4 - cls, pg = item & ((1u << sh) - 1), x = item >> sh;
+      if (*(volatile unsigned *)&h.bits[(size_t)x * h.words_per_chunk + (pg >> 5)] & (1u << (pg & 31))) {
+        set_error(h, OURO_ERR_DOUBLE_FREE, OURO_SITE_CHUNK_DOUBLE);
         cls = -1;
       }
     }
@@ -1770,7 +1998,11 @@ __device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, v
   __syncwarp(mask);
   if (held) stack_release<LOCKED>(ctx, w, cls);
   const unsigned rest = __ballot_sync(mask, cls >= 0 && rank >= take);
-  if (rest && ((rest >> lane) & 1)) page_free<V>(h, cls, item, rest);
+  if constexpr (ouro_page_queues(V)) {
+    if (rest && ((rest >> lane) & 1)) page_free<V>(h, cls, item, rest);
+  } else {
+    if (rest) chunk_or_run_free<V>(h, ((rest >> lane) & 1) ? cls : -1, item, p, mask);
+  }
 }
 template <int V, int WARPS>
 __device__ __forceinline__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
@@ -1807,6 +2039,22 @@ __device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev
       if (lane == 0) {
         ctx.cnt[w][c] = 0;
         /* these pages were counted as freed when they were staged */
+        stat_add(h, c, OURO_ST_FREE, 0ull - (unsigned long long)n);
+      }
+      __syncwarp();
+    }
+  } else {
+    /* chunk queues: the staged pages go back to their chunks (bits, counts,
+     * re-queued chunks), 32 lanes at a time */
+    for (unsigned c = 0; c < h.n_classes; ++c) {
+      const unsigned n = ctx.cnt[w][c];
+      if (!n) continue;
+      const bool mine = lane < n;
+      void *p = mine ? h.base + ((size_t)ctx.ids[w][c][lane] << (4 + c)) : nullptr;
+      chunk_free_impl<V>(h, mine ? (int)c : -1, p, 0xffffffffu);
+      __syncwarp();
+      if (lane == 0) {
+        ctx.cnt[w][c] = 0;
         stat_add(h, c, OURO_ST_FREE, 0ull - (unsigned long long)n);
       }
       __syncwarp();
@@ -1952,8 +2200,9 @@ static __device__ __noinline__ void ouro_free_warp(const ouro_heap_dev &h, void 
  * OURO_STAGE_CAP per class) and serves that warp's next malloc of the class
  * without a queue operation; ouro_block_end returns what is left to the class
  * queues.  A lane-private call takes the warp's class stack with a try-lock
- * bit (another lane holding it sends the request to the queues).  On chunk
- * queues the staged calls are the plain ones.  The block is one-dimensional
+ * bit (another lane holding it sends the request to the queues).  Chunk
+ * queues stage the same way (the page stays taken in its chunk's bitmap
+ * until ouro_block_end returns it).  The block is one-dimensional
  * with at most 32 * WARPS threads; a page freed through the staged form
  * must not be used by another block before ouro_block_end. */
 template <int WARPS>
@@ -1968,7 +2217,10 @@ __device__ void ouro_block_end(ouro_block_ctx<WARPS> &ctx) {
     case OURO_PAGE_ARRAY: ouro_block_end_v<OURO_PAGE_ARRAY, WARPS>(ctx, ctx.heap); break;
     case OURO_PAGE_VLIST: ouro_block_end_v<OURO_PAGE_VLIST, WARPS>(ctx, ctx.heap); break;
     case OURO_PAGE_VARRAY: ouro_block_end_v<OURO_PAGE_VARRAY, WARPS>(ctx, ctx.heap); break;
-    default: __syncthreads(); break;   /* chunk queues stage nothing */
+    case OURO_CHUNK_ARRAY: ouro_block_end_v<OURO_CHUNK_ARRAY, WARPS>(ctx, ctx.heap); break;
+    case OURO_CHUNK_VLIST: ouro_block_end_v<OURO_CHUNK_VLIST, WARPS>(ctx, ctx.heap); break;
+    case OURO_CHUNK_VARRAY: ouro_block_end_v<OURO_CHUNK_VARRAY, WARPS>(ctx, ctx.heap); break;
+    default: __syncthreads(); break;
   }
 }
 
@@ -1988,7 +2240,10 @@ __device__ __forceinline__ void *public_stage_malloc(ouro_block_ctx<WARPS> &ctx,
     case OURO_PAGE_ARRAY: return public_stage_malloc_v<OURO_PAGE_ARRAY, WARPS, FILL>(ctx, n, want, mask);
     case OURO_PAGE_VLIST: return public_stage_malloc_v<OURO_PAGE_VLIST, WARPS, FILL>(ctx, n, want, mask);
     case OURO_PAGE_VARRAY: return public_stage_malloc_v<OURO_PAGE_VARRAY, WARPS, FILL>(ctx, n, want, mask);
-    default: return public_malloc<FILL>(ctx.heap, n, want, mask);
+    case OURO_CHUNK_ARRAY: return public_stage_malloc_v<OURO_CHUNK_ARRAY, WARPS, FILL>(ctx, n, want, mask);
+    case OURO_CHUNK_VLIST: return public_stage_malloc_v<OURO_CHUNK_VLIST, WARPS, FILL>(ctx, n, want, mask);
+    case OURO_CHUNK_VARRAY: return public_stage_malloc_v<OURO_CHUNK_VARRAY, WARPS, FILL>(ctx, n, want, mask);
+    default: return nullptr;
   }
 }
 template <int WARPS>
@@ -1997,7 +2252,10 @@ __device__ __forceinline__ void public_stage_free(ouro_block_ctx<WARPS> &ctx, vo
     case OURO_PAGE_ARRAY: public_stage_free_v<OURO_PAGE_ARRAY, WARPS>(ctx, p, mask); break;
     case OURO_PAGE_VLIST: public_stage_free_v<OURO_PAGE_VLIST, WARPS>(ctx, p, mask); break;
     case OURO_PAGE_VARRAY: public_stage_free_v<OURO_PAGE_VARRAY, WARPS>(ctx, p, mask); break;
-    default: public_free(ctx.heap, p, mask); break;
+    case OURO_CHUNK_ARRAY: public_stage_free_v<OURO_CHUNK_ARRAY, WARPS>(ctx, p, mask); break;
+    case OURO_CHUNK_VLIST: public_stage_free_v<OURO_CHUNK_VLIST, WARPS>(ctx, p, mask); break;
+    case OURO_CHUNK_VARRAY: public_stage_free_v<OURO_CHUNK_VARRAY, WARPS>(ctx, p, mask); break;
+    default: break;
   }
 }
 }  // namespace detail

@@ -183,6 +183,86 @@ __global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *c
   }
 }
 
+/* Block-aggregated batch malloc for chunk queues (not the deoptimised
+ * form): every request takes its rank in its class's share of the block
+ * with one shared-memory atomic; one warp per class then obtains the whole
+ * share with chunk_acquire -- up to 32 queue positions per round, one per
+ * chunk, each lane reserving and claiming its chunk's part -- into a
+ * shared-memory page list, from which every request takes the page of its
+ * rank.  Requests above one chunk (runs) take the warp path of page_malloc.
+ * Statistics once per class per block. */
+template <int V, int R>
+__global__ void __launch_bounds__(256) k_batch_malloc_cblk(ouro_heap_dev h, const uint32_t *sizes, void **ptrs,
+                                                           size_t n) {
+  __shared__ unsigned s_cnt[OURO_MAX_CLASSES], s_got[OURO_MAX_CLASSES], s_base[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
+  __shared__ unsigned s_items[256 * R];
+  const size_t span = (size_t)blockDim.x * R;
+  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
+    uint32_t sz[R];
+    int cls[R];
+    unsigned long long pos[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t i = base + (size_t)r * blockDim.x + threadIdx.x;
+      sz[r] = i < n ? sizes[i] : 0;
+      cls[r] = i < n ? size_class(h, sz[r]) : -1;
+      if (i < n && cls[r] < 0) stat_add(h, OURO_ROW_NONE, sz[r] == 0 ? OURO_ST_ZERO : OURO_ST_TOO_LARGE, 1);
+    }
+    if (threadIdx.x < OURO_MAX_CLASSES) s_cnt[threadIdx.x] = s_ok[threadIdx.x] = 0;
+    __syncthreads();
+    int pc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) pc[r] = cls[r] < (int)h.n_classes ? cls[r] : -1;   /* runs: warp path below */
+    blk_reserve<R>(pc, pos, s_cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned acc = 0;
+      for (unsigned c = 0; c < h.n_classes; ++c) {
+        s_base[c] = acc;
+        acc += s_cnt[c];
+      }
+    }
+    __syncthreads();
+    for (unsigned c = warp; c < h.n_classes; c += nwarps)
+      if (s_cnt[c]) {
+        const unsigned got = chunk_acquire<V>(h, (int)c, s_cnt[c], s_items + s_base[c]);
+        if (lane == 0) s_got[c] = got;
+      }
+    __syncthreads();
+    void *res[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      res[r] = nullptr;
+      if (pc[r] >= 0 && pos[r] < s_got[pc[r]]) {
+        const unsigned item = s_items[s_base[pc[r]] + pos[r]];
+        if (item != OURO_NIL) {
+          res[r] = h.base + ((size_t)item << (4 + pc[r]));
+          atomicAdd(&s_ok[pc[r]], 1u);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {   /* runs above one chunk: the warp path */
+      const bool run = cls[r] >= (int)h.n_classes;
+      if (!__any_sync(0xffffffffu, run)) continue;
+      void *q = page_malloc<V>(h, run ? cls[r] : -1, 0xffffffffu);
+      if (run) res[r] = q;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t i = base + (size_t)r * blockDim.x + threadIdx.x;
+      if (i < n) ptrs[i] = res[r];
+    }
+    __syncthreads();
+    if (threadIdx.x < h.n_classes && s_cnt[threadIdx.x]) {
+      stat_add(h, threadIdx.x, OURO_ST_MALLOC, s_ok[threadIdx.x]);
+      stat_add(h, threadIdx.x, OURO_ST_FAILED, s_cnt[threadIdx.x] - s_ok[threadIdx.x]);
+    }
+    __syncthreads();
+  }
+}
+
 template <int OP>
 __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, uint32_t seed, int mode,
                           ouro_check *out) {
@@ -290,6 +370,17 @@ ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, s
         }
       }
       k_batch_malloc_blk<V, 1><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
+      OURO_LAUNCHED();
+      return OURO_OK;
+    }
+  }
+  if constexpr (!ouro_page_queues(V)) {
+    if (!H->d.deopt) {
+      if (blk_wide(n))
+        k_batch_malloc_cblk<V, BLK_WIDE><<<grid_for((n + BLK_WIDE - 1) / BLK_WIDE, block, 1 << 20), block, 0, s>>>(
+            H->d, d_sizes, d_ptrs, n);
+      else
+        k_batch_malloc_cblk<V, 1><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_sizes, d_ptrs, n);
       OURO_LAUNCHED();
       return OURO_OK;
     }

@@ -62,19 +62,17 @@ __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
   }
 }
 
-/* Staged malloc / free: page queues use the warp's shared-memory stacks;
- * chunk queues go to the heap. */
+/* Staged malloc / free: the warp's shared-memory stacks first (every queue
+ * form), then the heap. */
 template <int V, int WARPS>
 __device__ __forceinline__ void *stage_malloc_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h,
                                                 unsigned long long n, bool want) {
-  if constexpr (ouro_page_queues(V)) return ouro::detail::stage_malloc<V, WARPS>(ctx, h, n, want);
-  else return malloc_v<V>(h, n, want);
+  return ouro::detail::stage_malloc<V, WARPS>(ctx, h, n, want);
 }
 
 template <int V, int WARPS>
 __device__ __forceinline__ void stage_free_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p) {
-  if constexpr (ouro_page_queues(V)) ouro::detail::stage_free<V, WARPS>(ctx, h, p);
-  else free_v<V>(h, p);
+  ouro::detail::stage_free<V, WARPS>(ctx, h, p);
 }
 
 /* ------------------------------------------------------------- payload */

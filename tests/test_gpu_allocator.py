@@ -135,8 +135,9 @@ def test_sweep_per_launch(ouro, variant, threads):
 @pytest.mark.parametrize("variant", ALL_VARIANTS)
 def test_sweep_fused_rounds(ouro, variant, staging):
     """Fused rounds, with and without shared-memory staging of freed pages
-    (page queues; chunk queues ignore the option): counts and checksums
-    exact, and every staged page is back in its queue when the kernel ends."""
+    (every queue form): counts and checksums exact, and every staged page is
+    back in its queue (page queues) or its chunk (chunk queues) when the
+    kernel ends."""
     torch = torch_cuda()
     threads = 20000
     sizes = W.sweep_sizes(threads, seed=W.SEED_BASE + 12)
