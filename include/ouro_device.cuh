@@ -1621,8 +1621,10 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
     x = (unsigned)(off >> h.log2_chunk);
     pg = (unsigned)((off & (h.chunk_bytes - 1)) >> (4 + cls));
   }
-  /* 1. set the page bits, one atomicOr per (chunk, word) group */
-  __threadfence();
+  /* 1. set the page bits, one atomicOr per (chunk, word) group; the fence
+   * releases the block's data (and, after a warp barrier, the data other
+   * lanes wrote into it) before the page can be claimed again */
+  fence_acq_rel();
   const unsigned long long wkey = cls >= 0 ? (((unsigned long long)x << 32) | (pg >> 5)) : ~0ull;
   const unsigned wg = warp_group(h, mask, wkey);
   const unsigned bit = cls >= 0 ? 1u << (pg & 31) : 0u;
@@ -1639,8 +1641,10 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
   const unsigned cg = warp_group(h, mask, cls >= 0 ? x : OURO_NIL) & __ballot_sync(mask, cls >= 0);
   bool lift = false;
   if (cls >= 0 && lane == (unsigned)(__ffs(cg) - 1)) {
+    /* the count goes up after the bits are set (a reserving malloc that
+     * sees the count finds the bits, or waits for them in its claim) */
     const int k = __popc(cg);
-    __threadfence();
+    fence_acq_rel();
     const int b = atomicAdd(&h.chunk_free[x], k);
     lift = b <= 0 && b + k >= 1;
   }
