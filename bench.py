@@ -865,6 +865,17 @@ def extras(P, torch, np, heap, sizes, sizes_np, args, n, st, clk):
     except P.OuroError as e:
         ex["cuda_device_malloc"] = {"unavailable": str(e)}
 
+    # ---- the first round on a fresh heap (it carves every chunk) against warm rounds
+    with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=not args.no_staging) as hc:
+        oc = torch.zeros(5, dtype=torch.int64, device="cuda")
+        cold = timed(torch, stream, lambda: hc.round_fused(sizes, SEED, 1, out=oc))
+        okc = P.check_to_dict(oc) == want_chk
+        warm = timed(torch, stream, lambda: hc.round_fused(sizes, SEED, 1, out=oc), 5)
+        okc = okc and P.check_to_dict(oc) == want_chk and hc.stats()["error_bits"] == 0
+        ex["cold_round"] = {"first_round_ms": round(cold, 4), "warm_round_ms": round(warm, 4),
+                            "ratio": round(cold / warm, 2), "chunks_carved": int(sum(hc.stats()["carves"])),
+                            "verified": okc}
+
     # ---- the headline round with the other staging setting
     with P.Heap(HEAP_BYTES, CHUNK, args.variant, staging=args.no_staging) as h3:
         o3 = torch.zeros(5, dtype=torch.int64, device="cuda")

@@ -1610,8 +1610,11 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   return ret;
 }
 
-/* free into a chunk queue: every lane of mask calls; lanes with cls < 0 only take part */
-template <int V>
+/* free into a chunk queue: every lane of mask calls; lanes with cls < 0 only
+ * take part.  FENCE = false: the caller's blocks were written before the
+ * kernel began and no malloc runs in the same kernel (the batch free
+ * kernel), so no release is needed */
+template <int V, bool FENCE = true>
 __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, unsigned mask) {
   constexpr int QF = ouro_qform(V);
   const unsigned lane = laneid();
@@ -1624,7 +1627,7 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
   /* 1. set the page bits, one atomicOr per (chunk, word) group; the fence
    * releases the block's data (and, after a warp barrier, the data other
    * lanes wrote into it) before the page can be claimed again */
-  fence_acq_rel();
+  if (FENCE) fence_acq_rel();
   const unsigned long long wkey = cls >= 0 ? (((unsigned long long)x << 32) | (pg >> 5)) : ~0ull;
   const unsigned wg = warp_group(h, mask, wkey);
   const unsigned bit = cls >= 0 ? 1u << (pg & 31) : 0u;
@@ -1644,7 +1647,7 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
     /* the count goes up after the bits are set (a reserving malloc that
      * sees the count finds the bits, or waits for them in its claim) */
     const int k = __popc(cg);
-    fence_acq_rel();
+    if (FENCE) fence_acq_rel();
     const int b = atomicAdd(&h.chunk_free[x], k);
     lift = b <= 0 && b + k >= 1;
   }
@@ -1853,9 +1856,9 @@ __device__ void *chunk_or_run_malloc(const ouro_heap_dev &h, int cls, unsigned m
 }
 
 /* cls: the block's class, its run already marked free (runs), or -1 */
-template <int V>
+template <int V, bool FENCE = true>
 __device__ void chunk_or_run_free(const ouro_heap_dev &h, int cls, unsigned item, const void *p, unsigned mask) {
-  chunk_free_impl<V>(h, cls < (int)h.n_classes ? cls : -1, p, mask);
+  chunk_free_impl<V, FENCE>(h, cls < (int)h.n_classes ? cls : -1, p, mask);
   const unsigned rm = __ballot_sync(mask, cls >= (int)h.n_classes);
   if (rm && ((rm >> laneid()) & 1)) page_free<V>(h, cls, item, rm);
 }

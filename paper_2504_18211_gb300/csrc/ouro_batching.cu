@@ -27,7 +27,7 @@ namespace {
 constexpr unsigned TASK_REQ = 256;   /* requests per persistent task: 8 warp iterations */
 
 template <int V, bool STAGE>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, ouro_page_queues(V) ? 4 : 2)   /* chunk queues: no spills at 2 per SM */
 k_batches_persistent(ouro_heap_dev h, const uint32_t *sizes, const unsigned long long *offs,
                      const unsigned long long *task_offs, unsigned n_batches, uint32_t seed, int mode,
                      ouro_check *out, unsigned long long *work, unsigned long long n_tasks) {

@@ -28,7 +28,7 @@ __global__ void k_batch_malloc(ouro_heap_dev h, const uint32_t *sizes, void **pt
 template <int V>
 __global__ void k_batch_free(ouro_heap_dev h, void *const *ptrs, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    free_v<V>(h, ptrs[i]);
+    free_v<V, false>(h, ptrs[i]);   /* the blocks were written by earlier kernels */
 }
 
 /* Block-aggregated forms (page queues, not the deoptimised form): every
@@ -224,11 +224,15 @@ __global__ void __launch_bounds__(256) k_batch_malloc_cblk(ouro_heap_dev h, cons
       }
     }
     __syncthreads();
-    for (unsigned c = warp; c < h.n_classes; c += nwarps)
-      if (s_cnt[c]) {
-        const unsigned got = chunk_acquire<V>(h, (int)c, s_cnt[c], s_items + s_base[c]);
-        if (lane == 0) s_got[c] = got;
-      }
+    /* classes to warps: the largest classes (fewest pages per chunk, most
+     * positions to pop) get a warp each, the smallest share one in pairs */
+    const unsigned extra = h.n_classes > nwarps ? min(h.n_classes - nwarps, nwarps) : 0;
+    for (unsigned c = 0; c < h.n_classes; ++c) {
+      const unsigned wc = h.n_classes > 2 * nwarps ? c % nwarps : (c < 2 * extra ? c / 2 : c - extra);
+      if (wc != warp || !s_cnt[c]) continue;
+      const unsigned got = chunk_acquire<V>(h, (int)c, s_cnt[c], s_items + s_base[c]);
+      if (lane == 0) s_got[c] = got;
+    }
     __syncthreads();
     void *res[R];
 #pragma unroll
@@ -288,8 +292,10 @@ __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, ui
 #ifndef OURO_FUSED_MIN_BLOCKS
 #define OURO_FUSED_MIN_BLOCKS 4   /* resident blocks of 256 per SM the fused round is compiled for */
 #endif
+/* chunk queues: their larger malloc path gets 2 blocks of 256 per SM
+ * (128 registers a thread) instead of spilling at 64 */
 template <int V, bool STAGE>
-__global__ void __launch_bounds__(256, OURO_FUSED_MIN_BLOCKS) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
+__global__ void __launch_bounds__(256, ouro_page_queues(V) ? OURO_FUSED_MIN_BLOCKS : 2) k_round_fused(ouro_heap_dev h, const uint32_t *sizes, size_t n,
                                                      uint32_t seed, int mode, ouro_check *out, void **ptrs,
                                                      unsigned long long *work) {
   __shared__ ouro_block_ctx<8> ctx;

@@ -48,13 +48,15 @@ __device__ __forceinline__ int free_locate(const ouro_heap_dev &h, void *p, unsi
   return cls;
 }
 
-template <int V>
+/* FENCE = false: only for kernels that free blocks written before they began
+ * and allocate nothing (the batch free kernel) */
+template <int V, bool FENCE = true>
 __device__ __forceinline__ void free_v(const ouro_heap_dev &h, void *p) {
   const unsigned mask = __activemask();
   unsigned item = 0;
   const int cls = free_locate<V>(h, p, item);
   if constexpr (!ouro_page_queues(V)) {
-    chunk_or_run_free<V>(h, cls, item, p, mask);
+    chunk_or_run_free<V, FENCE>(h, cls, item, p, mask);
   } else {
     const unsigned vmask = __ballot_sync(mask, cls >= 0);
     if (cls < 0) return;
