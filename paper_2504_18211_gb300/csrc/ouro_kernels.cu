@@ -224,15 +224,11 @@ __global__ void __launch_bounds__(256) k_batch_malloc_cblk(ouro_heap_dev h, cons
       }
     }
     __syncthreads();
-    /* classes to warps: the largest classes (fewest pages per chunk, most
-     * positions to pop) get a warp each, the smallest share one in pairs */
-    const unsigned extra = h.n_classes > nwarps ? min(h.n_classes - nwarps, nwarps) : 0;
-    for (unsigned c = 0; c < h.n_classes; ++c) {
-      const unsigned wc = h.n_classes > 2 * nwarps ? c % nwarps : (c < 2 * extra ? c / 2 : c - extra);
-      if (wc != warp || !s_cnt[c]) continue;
-      const unsigned got = chunk_acquire<V>(h, (int)c, s_cnt[c], s_items + s_base[c]);
-      if (lane == 0) s_got[c] = got;
-    }
+    for (unsigned c = warp; c < h.n_classes; c += nwarps)
+      if (s_cnt[c]) {
+        const unsigned got = chunk_acquire<V>(h, (int)c, s_cnt[c], s_items + s_base[c]);
+        if (lane == 0) s_got[c] = got;
+      }
     __syncthreads();
     void *res[R];
 #pragma unroll
