@@ -198,9 +198,82 @@ enum {
   OURO_SITE_CHUNK_GIVEUP, OURO_SITE_CHUNK_DOUBLE, OURO_SITE_BAD_FREE, OURO_SITE_PAGE_DOUBLE,
   OURO_SITE_TRIM, OURO_SITE_GRAPH_LOCK, OURO_SITE_VA_NEW, OURO_SITE_VA_WAIT, OURO_SITE_RUN_FREE
 };
+}  // namespace detail
+}  // namespace ouro
+
+/* ---------------------------------------------------- debug event ring */
+/* Compile a kernel's translation unit with -DOURO_TRACE to record the slow
+ * events of the allocator it calls -- carves, null answers of an exhausted
+ * heap, new queue segments, bounded waits that ran out, errors -- in a ring
+ * of OURO_TRACE_CAP events kept in that translation unit's device memory.
+ * ouro_trace_copy (host) reads the newest events back.  Without
+ * OURO_TRACE the calls compile to nothing.  Debug aid only: every event
+ * takes one global atomic. */
+enum {
+  OURO_TR_CARVE = 1,       /* page or run carve: a = chunks taken, b = first producer position */
+  OURO_TR_CHUNK_CARVE,     /* chunk-queue carve batch: a = chunks taken, b = positions answered */
+  OURO_TR_EXHAUSTED,       /* positions answered null (no chunk left): a = count, b = first position */
+  OURO_TR_SEGMENT,         /* a queue segment set up: a = segment index, b = chunk */
+  OURO_TR_GIVEUP,          /* a bounded wait ran out: a = position, b = OURO_SITE_* */
+  OURO_TR_ERROR            /* an error bit was set: a = bits, b = OURO_SITE_* */
+};
+typedef struct {
+  unsigned long long t;    /* %globaltimer, ns */
+  unsigned kind, cls;      /* OURO_TR_*, size class (or ~0u) */
+  unsigned long long a, b;
+} ouro_trace_event;
+#ifdef OURO_TRACE
+#ifndef OURO_TRACE_CAP
+#define OURO_TRACE_CAP 4096   /* a power of two */
+#endif
+static __device__ ouro_trace_event ouro_trace_ring[OURO_TRACE_CAP];
+static __device__ unsigned long long ouro_trace_next;
+__device__ __forceinline__ void ouro_trace_event_put(unsigned kind, int cls, unsigned long long a,
+                                                     unsigned long long b) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  const unsigned long long i = atomicAdd(&ouro_trace_next, 1ull);
+  ouro_trace_event *e = &ouro_trace_ring[i & (OURO_TRACE_CAP - 1)];
+  e->t = t;
+  e->kind = kind;
+  e->cls = (unsigned)cls;
+  e->a = a;
+  e->b = b;
+}
+#define OURO_TRACE_EVENT(kind, cls, a, b) ouro_trace_event_put((kind), (cls), (a), (b))
+/* Host: the newest min(total, OURO_TRACE_CAP, cap) events of this
+ * translation unit's ring, oldest first, into out; *total = events ever
+ * recorded.  Synchronous (cudaMemcpyFromSymbol); call when the kernels that
+ * record are done.  Clears the ring when clear != 0. */
+static inline __host__ cudaError_t ouro_trace_copy(ouro_trace_event *out, unsigned cap, unsigned long long *total,
+                                                   int clear) {
+  unsigned long long n = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&n, ouro_trace_next, sizeof(n));
+  if (e != cudaSuccess) return e;
+  if (total) *total = n;
+  const unsigned long long keep = n < OURO_TRACE_CAP ? n : OURO_TRACE_CAP;
+  const unsigned long long want = keep < cap ? keep : cap;
+  for (unsigned long long k = 0; k < want; ++k) {
+    const unsigned long long i = (n - want + k) & (OURO_TRACE_CAP - 1);
+    e = cudaMemcpyFromSymbol(out + k, ouro_trace_ring, sizeof(ouro_trace_event), i * sizeof(ouro_trace_event));
+    if (e != cudaSuccess) return e;
+  }
+  if (clear) {
+    const unsigned long long zero = 0;
+    e = cudaMemcpyToSymbol(ouro_trace_next, &zero, sizeof(zero));
+  }
+  return e;
+}
+#else
+#define OURO_TRACE_EVENT(kind, cls, a, b) ((void)0)
+#endif
+
+namespace ouro {
+namespace detail {
 __device__ __forceinline__ void set_error(const ouro_heap_dev &h, unsigned bits, unsigned site) {
   atomicOr(&gl(h)->error_bits, bits);
   atomicCAS(&gl(h)->error_site, 0u, site);
+  OURO_TRACE_EVENT(OURO_TR_ERROR, -1, bits, site);
 }
 
 /* power-of-two class: ceil(log2 n) - 4, floor 16 B; -1 for 0 or above
@@ -357,6 +430,7 @@ __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) 
     stat_add(h, c, OURO_ST_SEG, 1);
   }
   seg_init(h, x, idx, fresh);
+  OURO_TRACE_EVENT(OURO_TR_SEGMENT, c, idx, x);
   return x;
 }
 
@@ -829,6 +903,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
         t0 = atomicAdd(&q->tail.v, (unsigned long long)m << ppc_log);
         atomicAdd(&q->carved.v, (unsigned long long)m);
         stat_add(h, c, OURO_ST_CARVE, m);
+        OURO_TRACE_EVENT(OURO_TR_CARVE, c, m, t0);
       }
     }
   }
@@ -895,6 +970,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
         if (atomicCAS(&q->tail.v, t, hd) == t) { dt = t; dn = hd - t; break; }
       }
       stat_add(h, c, OURO_ST_DEAD, dn);
+      if (dn) OURO_TRACE_EVENT(OURO_TR_EXHAUSTED, c, dn, dt);
     }
     dt = __shfl_sync(vmask, dt, owner);
     dn = __shfl_sync(vmask, dn, owner);
@@ -948,6 +1024,7 @@ __device__ __noinline__ void run_carve(const ouro_heap_dev &h, int c, unsigned v
       if (m) {
         t0 = atomicAdd(&q->tail.v, m);
         stat_add(h, c, OURO_ST_CARVE, m << k_log);
+        OURO_TRACE_EVENT(OURO_TR_CARVE, c, m << k_log, t0);
       }
     }
   }
@@ -983,6 +1060,7 @@ __device__ __noinline__ void run_carve(const ouro_heap_dev &h, int c, unsigned v
         if (atomicCAS(&q->tail.v, t, hd) == t) { dt = t; dn = hd - t; break; }
       }
       stat_add(h, c, OURO_ST_DEAD, dn);
+      if (dn) OURO_TRACE_EVENT(OURO_TR_EXHAUSTED, c, dn, dt);
     }
     dt = __shfl_sync(vmask, dt, owner);
     dn = __shfl_sync(vmask, dn, owner);
@@ -1069,6 +1147,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, un
           if (st == 3) {
             set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_PAGE_GIVEUP);
             stat_add(h, cls, OURO_ST_CANCEL, 1);
+            OURO_TRACE_EVENT(OURO_TR_GIVEUP, cls, pos, OURO_SITE_PAGE_GIVEUP);
           }
         }
         break;
@@ -1312,6 +1391,7 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
     if ((int)lane == owner) {
       cr = take_chunks(h, m);
       if (cr.k1 + cr.k2) stat_add(h, c, OURO_ST_CARVE, cr.k1 + cr.k2);
+      OURO_TRACE_EVENT(OURO_TR_CHUNK_CARVE, c, cr.k1 + cr.k2, D);
     }
     cr.p0 = __shfl_sync(vmask, cr.p0, owner);
     cr.b0 = __shfl_sync(vmask, cr.b0, owner);
@@ -1382,6 +1462,7 @@ __device__ __noinline__ void chunk_carve(const ouro_heap_dev &h, int c, unsigned
           if (atomicCAS(&q->tail.v, t2, h2) == t2) { dt = t2; dn = h2 - t2; break; }
         }
         stat_add(h, c, OURO_ST_DEAD, dn);
+        if (dn) OURO_TRACE_EVENT(OURO_TR_EXHAUSTED, c, dn, dt);
       }
       dt = __shfl_sync(vmask, dt, owner);
       dn = __shfl_sync(vmask, dn, owner);

@@ -19,7 +19,8 @@ def pytest_configure(config):
 def pytest_collection_finish(session):
     """GPU tests of the public device API need the test-only user-kernel
     library: start its build now, so that it overlaps the other tests."""
-    if any("test_gpu_user_api" in item.nodeid and item.get_closest_marker("gpu") for item in session.items):
+    if any(("test_gpu_user_api" in item.nodeid or "test_gpu_trace" in item.nodeid) and item.get_closest_marker("gpu")
+           for item in session.items):
         sys.path.insert(0, os.path.join(TESTS, "cuda"))
         import build_user
         build_user.start_background()

@@ -1,9 +1,10 @@
 """Build the test-only library of user kernels (libouro_user.so, sm_103a).
 
-Its two kernel files (ouro_user_plain.cu, ouro_user_staged.cu) include only
-the public device header include/ouro_device.cuh, as an application's
-kernels would; each compiles twice (lane-private and warp-collective calls),
-the four objects in parallel.  The GPU tests start this build in
+Its kernel files include only the public device header
+include/ouro_device.cuh, as an application's kernels would:
+ouro_user_plain.cu and ouro_user_staged.cu compile twice each (lane-private
+and warp-collective calls), ouro_user_trace.cu once with the device event
+ring (-DOURO_TRACE); the five objects compile in parallel.  The GPU tests start this build in
 the background when the session collects them (tests/conftest.py), so that
 it overlaps the other GPU tests, and wait for it before their first call.
 """
@@ -19,8 +20,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libouro_user.so")
-SOURCES = ("ouro_user_plain.cu", "ouro_user_staged.cu")
-JOBS = [(src, coll) for src in SOURCES for coll in (0, 1)]   # lane-private / warp-collective
+SOURCES = ("ouro_user_plain.cu", "ouro_user_staged.cu", "ouro_user_trace.cu")
+# (source, object tag, flags): the two round files for lane-private and
+# warp-collective calls, the trace file with the device event ring on
+JOBS = [(src, str(coll), [f"-DUT_COLLECTIVE={coll}"]) for src in SOURCES[:2] for coll in (0, 1)] + \
+       [("ouro_user_trace.cu", "trace", ["-DOURO_TRACE"])]
 DEPS = SOURCES + ("ouro_user_common.cuh", "build_user.py")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -47,10 +51,10 @@ def build(force: bool = False) -> str:
     os.makedirs(out_dir, exist_ok=True)
 
     def compile_one(job):
-        src, coll = job
-        obj = os.path.join(out_dir, f"{os.path.splitext(src)[0]}.{coll}.o")
+        src, tag, flags = job
+        obj = os.path.join(out_dir, f"{os.path.splitext(src)[0]}.{tag}.o")
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-split-compile", "0", "-Xcompiler", "-fPIC",
-               f"-DUT_COLLECTIVE={coll}", "-I", INCLUDE, "-I", HERE, "-c", os.path.join(HERE, src), "-o", obj]
+               *flags, "-I", INCLUDE, "-I", HERE, "-c", os.path.join(HERE, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
