@@ -1124,8 +1124,12 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, un
       }
       const unsigned dmask = __ballot_sync(vmask, debt);
       if (dmask) {
-        const unsigned same = __match_any_sync(vmask, debt ? cls : -1);
-        const bool trier = debt && lane == (unsigned)(__ffs(same) - 1);
+        /* one lock attempt per warp, for the class of its lowest lane in
+         * debt: a warp carves one class at a time, and the lock holder
+         * carves the whole debt of its class, so the classes of a cold heap
+         * are carved by different warps at once (a warp that took the locks
+         * of several classes carved them in turn while the others waited) */
+        const bool trier = debt && lane == (unsigned)(__ffs(dmask) - 1);
         const bool got = trier && try_lock(&q->lock.v);
         unsigned lockers = __ballot_sync(vmask, got);
         while (lockers) {
@@ -1608,7 +1612,7 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
     /* carve: one lock taker per class among the debtors of the warp */
     const unsigned dmask = __ballot_sync(vmask, debt);
     if (dmask) {
-      const bool got = debt && try_lock(&q->lock.v);
+      const bool got = debt && lane == (unsigned)(__ffs(dmask) - 1) && try_lock(&q->lock.v);   /* see page_malloc */
       unsigned lockers = __ballot_sync(vmask, got);
       while (lockers) {
         const int j = __ffs(lockers) - 1;

@@ -288,12 +288,6 @@ __global__ void k_pattern(void *const *ptrs, const uint32_t *sizes, size_t n, ui
 #ifndef OURO_FUSED_MIN_BLOCKS
 #define OURO_FUSED_MIN_BLOCKS 4   /* resident blocks of 256 per SM the fused round is compiled for */
 #endif
-#ifndef OURO_FUSED_TASK_ROUNDS
-#define OURO_FUSED_TASK_ROUNDS 1  /* rounds of 32 requests per task a warp claims */
-#endif
-#ifndef OURO_FUSED_PREFETCH
-#define OURO_FUSED_PREFETCH 1     /* claim the next task while the current one runs */
-#endif
 /* chunk queues: their larger malloc path gets 2 blocks of 256 per SM
  * (128 registers a thread) instead of spilling at 64 */
 template <int V, bool STAGE>
@@ -305,42 +299,29 @@ __global__ void __launch_bounds__(256, ouro_page_queues(V) ? OURO_FUSED_MIN_BLOC
   payload_acc a;
   unsigned long long nulls = 0;
   const unsigned lane = threadIdx.x & 31;
-  constexpr unsigned long long TASK = 32ull * OURO_FUSED_TASK_ROUNDS;
-  unsigned long long next = 0;
-  if (lane == 0) next = atomicAdd(work, TASK);
-  next = __shfl_sync(0xffffffffu, next, 0);
   for (;;) {
-    const unsigned long long base = next;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, 32ull);
+    base = __shfl_sync(0xffffffffu, base, 0);
     if (base >= n) break;
-#if OURO_FUSED_PREFETCH
-    if (lane == 0) next = atomicAdd(work, TASK);   /* the next task's claim, in flight during this one */
-#endif
-    for (unsigned r = 0; r < OURO_FUSED_TASK_ROUNDS; ++r) {
-      const unsigned long long rb = base + 32ull * r;
-      if (rb >= n) break;
-      const size_t i = rb + lane;
-      const uint32_t sz = i < n ? sizes[i] : 0;
-      unsigned char *p = nullptr;
-      if (STAGE) {
-        p = static_cast<unsigned char *>(stage_malloc_v<V>(ctx, h, sz, i < n));
-      } else if (i < n) {
-        p = static_cast<unsigned char *>(malloc_v<V>(h, sz));
-      }
-      if (i < n) {
-        if (!p) nulls++;
-        if (ptrs) ptrs[i] = p;
-      }
-      __syncwarp();
-      warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed, mode, a);
-      __syncwarp();
-      if (STAGE) stage_free_v<V>(ctx, h, p);
-      else if (i < n) free_v<V>(h, p);
-      __syncwarp();
+    const size_t i = base + lane;
+    const uint32_t sz = i < n ? sizes[i] : 0;
+    unsigned char *p = nullptr;
+    if (STAGE) {
+      p = static_cast<unsigned char *>(stage_malloc_v<V>(ctx, h, sz, i < n));
+    } else if (i < n) {
+      p = static_cast<unsigned char *>(malloc_v<V>(h, sz));
     }
-#if !OURO_FUSED_PREFETCH
-    if (lane == 0) next = atomicAdd(work, TASK);
-#endif
-    next = __shfl_sync(0xffffffffu, next, 0);
+    if (i < n) {
+      if (!p) nulls++;
+      if (ptrs) ptrs[i] = p;
+    }
+    __syncwarp();
+    warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed, mode, a);
+    __syncwarp();
+    if (STAGE) stage_free_v<V>(ctx, h, p);
+    else if (i < n) free_v<V>(h, p);
+    __syncwarp();
   }
   if (STAGE) ouro_block_end_v<V>(ctx, h);
   flush_acc(a, nulls, out);
