@@ -24,9 +24,10 @@
  *     so a warp group needs ONE atomic on head (malloc) or tail (free) and its
  *     lanes then touch consecutive slots (coalesced);
  *   - a consumer whose position is beyond the producers is "in debt": the
- *     one lane per class that takes the class carve lock carves every chunk
- *     the current debt needs in one batch, and its whole warp writes the new
- *     page ids into the slots;
+ *     one lane per class that takes the class carve lock carves the chunks
+ *     the current debt needs, at most 4096 pages' worth, releases the lock
+ *     and its whole warp writes the new page ids into the slots, so that
+ *     other warps in debt carve and fill the rest at the same time;
  *   - when the heap has no chunk left, the remaining debt positions are
  *     answered with a null marker, so a full heap returns null exactly as
  *     often as a sequential allocator would in a malloc-only phase.
@@ -52,6 +53,7 @@
 #define OURO_SHARDS 32
 #define OURO_SEG_HDR 64
 #define OURO_AHEAD_POS (1ull << 20)   /* recycled segments go at most this many positions past the tail */
+#define OURO_CARVE_SLOTS 4096u        /* slots one page carve fills at most (one chunk at least) */
 
 /* queue storage forms */
 #define OURO_QF_RING 0     /* plain array: a ring of slots outside the heap */
@@ -865,10 +867,14 @@ __device__ inline void push_one(const ouro_heap_dev &h, int c, unsigned item) {
 
 /* ---------------------------------------------- page queues: carve batch */
 /* Called by every lane of vmask; lane `owner` holds the carve lock of class
- * c and releases it.  Carves the chunks the class's current debt needs (one
- * batch), then the warp writes the new page ids into the debt slots.  If the
- * heap (or the page-array capacity) is exhausted, the remaining debt slots
- * get the null marker. */
+ * c and releases it.  Carves the chunks the class's current debt needs, up
+ * to OURO_CARVE_SLOTS pages (one batch), then the warp writes the new page
+ * ids into the debt slots.  If the heap (or the page-array capacity) is
+ * exhausted, the remaining debt slots get the null marker.  The lock covers
+ * only the reservation (chunks taken, tail advanced, or the tail moved to
+ * the head with null answers): it is released before the slots are
+ * written, so that the next warp in debt carves the next batch of the class
+ * while this one fills, and a large debt is filled by many warps at once. */
 template <int V, int FILL = 1>
 __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int owner) {
   constexpr int QF = ouro_qform(V);
@@ -886,6 +892,7 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
     if (hd > t) {
       unsigned long long want = (hd - t + ppc - 1) >> ppc_log;
       unsigned long long ask = min(want, (unsigned long long)h.max_carve);
+      ask = min(ask, max(1ull, (unsigned long long)(OURO_CARVE_SLOTS >> ppc_log)));
       if (V == OURO_PAGE_ARRAY) {
         unsigned long long limit = h.qcap[c] >> ppc_log, have = ld_rlx(&q->carved.v);
         ask = have >= limit ? 0 : min(ask, limit - have);
@@ -907,8 +914,22 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
       }
     }
   }
+  unsigned long long dt = 0, dn = 0;
+  if ((int)lane == owner) {
+    if (exhausted) {   /* every position still in debt gets the null answer */
+      for (unsigned it = 0; it < h.spin_limit; ++it) {
+        unsigned long long t = ld_acq(&q->tail.v), hd = ld_acq(&q->head.v);
+        if (hd <= t) break;
+        if (atomicCAS(&q->tail.v, t, hd) == t) { dt = t; dn = hd - t; break; }
+      }
+      stat_add(h, c, OURO_ST_DEAD, dn);
+      if (dn) OURO_TRACE_EVENT(OURO_TR_EXHAUSTED, c, dn, dt);
+    }
+    unlock(&q->lock.v);
+  }
   m = __shfl_sync(vmask, m, owner);
-  exhausted = __shfl_sync(vmask, exhausted, owner);
+  dt = __shfl_sync(vmask, dt, owner);
+  dn = __shfl_sync(vmask, dn, owner);
   t0 = __shfl_sync(vmask, t0, owner);
   r.p0 = __shfl_sync(vmask, r.p0, owner);
   r.b0 = __shfl_sync(vmask, r.b0, owner);
@@ -961,29 +982,14 @@ __device__ void page_carve(const ouro_heap_dev &h, int c, unsigned vmask, int ow
       }
     }
   }
-  if (exhausted) {
-    unsigned long long dt = 0, dn = 0;
-    if ((int)lane == owner) {
-      for (unsigned it = 0; it < h.spin_limit; ++it) {
-        unsigned long long t = ld_acq(&q->tail.v), hd = ld_acq(&q->head.v);
-        if (hd <= t) break;
-        if (atomicCAS(&q->tail.v, t, hd) == t) { dt = t; dn = hd - t; break; }
-      }
-      stat_add(h, c, OURO_ST_DEAD, dn);
-      if (dn) OURO_TRACE_EVENT(OURO_TR_EXHAUSTED, c, dn, dt);
-    }
-    dt = __shfl_sync(vmask, dt, owner);
-    dn = __shfl_sync(vmask, dn, owner);
-    for (unsigned long long i0 = 0; i0 < dn; i0 += nl) {
-      const unsigned long long i = i0 + rk;
-      const bool act = i < dn;
-      unsigned long long *cell = act ? slot_at<QF>(h, c, dt + i, true) : nullptr;
-      if (cell) put_at(h, cell, dt + i, 0, true, VL);
-      if (VL) seg_event_warp<QF>(h, c, cell, act, vmask);
-    }
+  for (unsigned long long i0 = 0; i0 < dn; i0 += nl) {
+    const unsigned long long i = i0 + rk;
+    const bool act = i < dn;
+    unsigned long long *cell = act ? slot_at<QF>(h, c, dt + i, true) : nullptr;
+    if (cell) put_at(h, cell, dt + i, 0, true, VL);
+    if (VL) seg_event_warp<QF>(h, c, cell, act, vmask);
   }
   __syncwarp(vmask);
-  if ((int)lane == owner) unlock(&q->lock.v);
 }
 
 /* ------------------------------------------- run queues: carve batch */
