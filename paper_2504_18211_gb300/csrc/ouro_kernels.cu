@@ -185,17 +185,25 @@ __global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *c
 
 /* Block-aggregated batch malloc for chunk queues (not the deoptimised
  * form): every request takes its rank in its class's share of the block
- * with one shared-memory atomic; one warp per class then obtains the whole
- * share with chunk_acquire -- up to 32 queue positions per round, one per
- * chunk, each lane reserving and claiming its chunk's part -- into a
- * shared-memory page list, from which every request takes the page of its
- * rank.  Requests above one chunk (runs) take the warp path of page_malloc.
+ * with one shared-memory atomic; the shares are cut into tasks of at most
+ * 32 whole chunks' pages (what one round of chunk_acquire serves from a
+ * queue of whole chunks: 32 queue positions, each lane reserving and
+ * claiming its chunk's part), and the block's warps take the tasks in turn,
+ * classes with the fewest pages per chunk first, into a shared-memory page
+ * list from which every request takes the page of its rank.  A class of
+ * one page per chunk thus spreads over several warps instead of costing
+ * one warp a round per 32 requests while the others wait at the barrier.
+ * Requests above one chunk (runs) take the warp path of page_malloc.
  * Statistics once per class per block. */
 template <int V, int R>
 __global__ void __launch_bounds__(256) k_batch_malloc_cblk(ouro_heap_dev h, const uint32_t *sizes, void **ptrs,
                                                            size_t n) {
-  __shared__ unsigned s_cnt[OURO_MAX_CLASSES], s_got[OURO_MAX_CLASSES], s_base[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
+  static_assert(256 * R < 2048, "task offsets and counts are 11-bit fields");
+  constexpr unsigned MAX_TASKS = (256 * R) / 32 + OURO_MAX_CLASSES;   /* sum over classes of ceil(share / part) */
+  __shared__ unsigned s_cnt[OURO_MAX_CLASSES], s_base[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
   __shared__ unsigned s_items[256 * R];
+  __shared__ unsigned s_task[MAX_TASKS];   /* class | offset << 5 | count << 16 */
+  __shared__ unsigned s_ntask;
   const size_t span = (size_t)blockDim.x * R;
   const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
@@ -217,24 +225,31 @@ __global__ void __launch_bounds__(256) k_batch_malloc_cblk(ouro_heap_dev h, cons
     blk_reserve<R>(pc, pos, s_cnt);
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned acc = 0;
+      unsigned acc = 0, nt = 0;
       for (unsigned c = 0; c < h.n_classes; ++c) {
         s_base[c] = acc;
         acc += s_cnt[c];
       }
+      for (int c = (int)h.n_classes - 1; c >= 0; --c) {
+        const unsigned part = 32u << (h.log2_chunk - 4 - c);
+        for (unsigned o = 0; o < s_cnt[c]; o += part)
+          s_task[nt++] = (unsigned)c | (o << 5) | (min(part, s_cnt[c] - o) << 16);
+      }
+      s_ntask = nt;
     }
     __syncthreads();
-    for (unsigned c = warp; c < h.n_classes; c += nwarps)
-      if (s_cnt[c]) {
-        const unsigned got = chunk_acquire<V>(h, (int)c, s_cnt[c], s_items + s_base[c]);
-        if (lane == 0) s_got[c] = got;
-      }
+    for (unsigned t = warp; t < s_ntask; t += nwarps) {
+      const unsigned tk = s_task[t], c = tk & 31u, cnt = tk >> 16;
+      unsigned *out = s_items + s_base[c] + ((tk >> 5) & 2047u);
+      const unsigned got = chunk_acquire<V>(h, (int)c, cnt, out);
+      for (unsigned i = got + lane; i < cnt; i += 32) out[i] = OURO_NIL;   /* the heap ran out: null answers */
+    }
     __syncthreads();
     void *res[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       res[r] = nullptr;
-      if (pc[r] >= 0 && pos[r] < s_got[pc[r]]) {
+      if (pc[r] >= 0) {
         const unsigned item = s_items[s_base[pc[r]] + pos[r]];
         if (item != OURO_NIL) {
           res[r] = h.base + ((size_t)item << (4 + pc[r]));
