@@ -1701,15 +1701,18 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
   return ret;
 }
 
-/* free into a chunk queue: every lane of mask calls; lanes with cls < 0 only
- * take part.  FENCE = false: the caller's blocks were written before the
- * kernel began and no malloc runs in the same kernel (the batch free
- * kernel), so no release is needed */
-template <int V, bool FENCE = true>
-__device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, unsigned mask) {
-  constexpr int QF = ouro_qform(V);
+/* The release half of a chunk-queue free: every lane of mask calls; lanes
+ * with cls < 0 only take part.  Sets the page's bit and counts it back on
+ * its chunk; true for the lane whose count increment lifted the chunk from
+ * <= 0 to >= 1 (that lane queues chunk x).  cls turns to -1 on a double
+ * free (recorded).  FENCE = false: the caller's blocks were written before
+ * the kernel began and no malloc runs in the same kernel (the batch free
+ * kernels), so no release is needed */
+template <bool FENCE = true>
+__device__ bool chunk_release(const ouro_heap_dev &h, int &cls, const void *p, unsigned mask, unsigned &x) {
   const unsigned lane = laneid();
-  unsigned x = 0, pg = 0;
+  unsigned pg = 0;
+  x = 0;
   if (cls >= 0) {
     const unsigned long long off = (unsigned long long)((const unsigned char *)p - h.base);
     x = (unsigned)(off >> h.log2_chunk);
@@ -1742,6 +1745,17 @@ __device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, 
     const int b = atomicAdd(&h.chunk_free[x], k);
     lift = b <= 0 && b + k >= 1;
   }
+  return lift;
+}
+
+/* free into a chunk queue: every lane of mask calls; lanes with cls < 0 only
+ * take part (FENCE as for chunk_release) */
+template <int V, bool FENCE = true>
+__device__ void chunk_free_impl(const ouro_heap_dev &h, int cls, const void *p, unsigned mask) {
+  constexpr int QF = ouro_qform(V);
+  const unsigned lane = laneid();
+  unsigned x;
+  const bool lift = chunk_release<FENCE>(h, cls, p, mask, x);
   push_group<QF>(h, cls, x, lift, mask);   /* the lifted chunks, one tail atomic per class */
   const unsigned sg = warp_group(h, mask, cls);
   if (cls >= 0 && lane == (unsigned)(__ffs(sg) - 1)) stat_add(h, cls, OURO_ST_FREE, __popc(sg));

@@ -183,6 +183,69 @@ __global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *c
   }
 }
 
+/* Block-aggregated batch free for chunk queues (not the deoptimised form):
+ * each request sets its page bit and counts it back on its chunk with its
+ * warp, as a single free does (one atomicOr per (chunk, word) group, one
+ * count atomic per chunk group); the chunks whose count that lifted take
+ * their rank in their class's share of the block with one shared-memory
+ * atomic, and one thread per class takes the block's tail positions with a
+ * single global atomic.  Per warp, those tail atomics piled up on the class
+ * of one page per chunk, where every free lifts a chunk.  Statistics once
+ * per class per block; runs above one chunk take the warp path. */
+template <int V, int R>
+__global__ void __launch_bounds__(256) k_batch_free_cblk(ouro_heap_dev h, void *const *ptrs, size_t n) {
+  __shared__ unsigned s_cnt[OURO_MAX_CLASSES], s_free[OURO_MAX_CLASSES];
+  __shared__ unsigned long long s_pos[OURO_MAX_CLASSES];
+  const size_t span = (size_t)blockDim.x * R;
+  for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
+    void *p[R];
+    unsigned item[R], x[R];
+    int cls[R];
+    bool lift[R];
+    unsigned long long pos[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const size_t i = base + (size_t)r * blockDim.x + threadIdx.x;
+      p[r] = i < n ? ptrs[i] : nullptr;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      item[r] = 0;
+      cls[r] = free_locate<V>(h, p[r], item[r]);   /* a run is marked free here */
+    }
+    if (threadIdx.x < OURO_MAX_CLASSES) s_cnt[threadIdx.x] = s_free[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      int pc = cls[r] < (int)h.n_classes ? cls[r] : -1;
+      lift[r] = chunk_release<false>(h, pc, p[r], 0xffffffffu, x[r]);   /* pc: -1 on a double free */
+      if (cls[r] < (int)h.n_classes) cls[r] = pc;
+      if (pc >= 0) atomicAdd(&s_free[pc], 1u);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) pos[r] = lift[r] ? atomicAdd(&s_cnt[cls[r]], 1u) : 0u;
+    __syncthreads();
+    if (threadIdx.x < h.n_classes) {
+      if (s_cnt[threadIdx.x])
+        s_pos[threadIdx.x] = atomicAdd(&qh(h, threadIdx.x)->tail.v, (unsigned long long)s_cnt[threadIdx.x]);
+      if (s_free[threadIdx.x]) stat_add(h, threadIdx.x, OURO_ST_FREE, s_free[threadIdx.x]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {   /* the lifted chunks into their class queues, at the taken positions */
+      const unsigned vmask = __ballot_sync(0xffffffffu, lift[r]);
+      if (lift[r]) page_free<V, true>(h, cls[r], x[r], vmask, s_pos[cls[r]] + pos[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {   /* runs above one chunk: the warp path */
+      const bool run = cls[r] >= (int)h.n_classes;
+      const unsigned rm = __ballot_sync(0xffffffffu, run);
+      if (run) page_free<V>(h, cls[r], item[r], rm);
+    }
+    __syncthreads();
+  }
+}
+
 /* Block-aggregated batch malloc for chunk queues (not the deoptimised
  * form): every request takes its rank in its class's share of the block
  * with one shared-memory atomic; the shares are cut into tasks of at most
@@ -421,6 +484,17 @@ ouro_status batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, cudaStream_t
         }
       }
       k_batch_free_blk<V, 1><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
+      OURO_LAUNCHED();
+      return OURO_OK;
+    }
+  }
+  if constexpr (!ouro_page_queues(V)) {
+    if (!H->d.deopt) {
+      if (blk_wide(n))
+        k_batch_free_cblk<V, BLK_WIDE><<<grid_for((n + BLK_WIDE - 1) / BLK_WIDE, block, 1 << 20), block, 0, s>>>(
+            H->d, d_ptrs, n);
+      else
+        k_batch_free_cblk<V, 1><<<grid_for(n, block, 1 << 20), block, 0, s>>>(H->d, d_ptrs, n);
       OURO_LAUNCHED();
       return OURO_OK;
     }
