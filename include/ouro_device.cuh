@@ -1632,50 +1632,40 @@ __device__ void *chunk_malloc(const ouro_heap_dev &h, int cls, unsigned vmask) {
     got_item = __shfl_sync(vmask, got_item, gl_leader);
     const unsigned any = __ballot_sync(vmask, mine && res != 0);
     if (mine && res == 2) st = 2;
-    /* groups holding a chunk: reserve and claim pages (all lanes of vmask take part) */
-    unsigned work = any;
-    while (work) {
-      const int j = __ffs(work) - 1;
-      const unsigned jg = __shfl_sync(vmask, gmask, j);
-      work &= ~jg;
-      const unsigned jres = __shfl_sync(vmask, res, j);
-      if (jres != 1) continue;
-      const unsigned jitem = __shfl_sync(vmask, got_item, j);
-      const unsigned jneed = __popc(jg);
-      const unsigned jleader = __ffs(jg) - 1;
-      const int jcls = __shfl_sync(vmask, cls, j);
-      const unsigned jppc = 1u << (h.log2_chunk - 4 - jcls);
-      const unsigned x = OURO_CQ_ID(jitem);
-      unsigned granted = 0;
-      if (lane == jleader) {
-        if (jitem & OURO_CQ_RES) {
-          const unsigned cnt = OURO_CQ_CNT(jitem);
-          granted = min(cnt, jneed);
-          if (cnt > jneed) {   /* reserved for a warp-sized need that was not posted: hand back the rest */
-            const int ex = (int)(cnt - jneed);
-            const int b = atomicAdd(&h.chunk_free[x], ex);
-            if (b <= 0 && b + ex >= 1) chunk_push<QF>(h, jcls, x);
-          }
-        } else {
-          const int old = atomicSub(&h.chunk_free[x], (int)jneed);
-          granted = old <= 0 ? 0 : min((unsigned)old, jneed);
-          const int left = old - (int)jneed;
-          if (left >= 1) chunk_push<QF>(h, jcls, x);
-          if (granted < jneed) {
-            const int ex = (int)(jneed - granted);
-            const int b = atomicAdd(&h.chunk_free[x], ex);
-            if (b <= 0 && b + ex >= 1) chunk_push<QF>(h, jcls, x);
-          }
+    /* groups holding a chunk reserve and claim pages, every group at once:
+     * the leaders' count atomics (and pushes) are issued together, then each
+     * group claims from its own chunk with collectives over its own lanes */
+    const bool holder = mine && res == 1;            /* uniform within a group */
+    unsigned granted = 0, x = 0;
+    if (holder && lane == leader) {
+      x = OURO_CQ_ID(got_item);
+      if (got_item & OURO_CQ_RES) {
+        const unsigned cnt = OURO_CQ_CNT(got_item);
+        granted = min(cnt, need);
+        if (cnt > need) {   /* reserved for a warp-sized need that was not posted: hand back the rest */
+          const int ex = (int)(cnt - need);
+          const int b = atomicAdd(&h.chunk_free[x], ex);
+          if (b <= 0 && b + ex >= 1) chunk_push<QF>(h, cls, x);
+        }
+      } else {
+        const int old = atomicSub(&h.chunk_free[x], (int)need);
+        granted = old <= 0 ? 0 : min((unsigned)old, need);
+        const int left = old - (int)need;
+        if (left >= 1) chunk_push<QF>(h, cls, x);
+        if (granted < need) {
+          const int ex = (int)(need - granted);
+          const int b = atomicAdd(&h.chunk_free[x], ex);
+          if (b <= 0 && b + ex >= 1) chunk_push<QF>(h, cls, x);
         }
       }
-      granted = __shfl_sync(vmask, granted, jleader);
-      const bool in_g = (jg >> lane) & 1;
-      const unsigned jrank = __popc(jg & lanemask_lt());
-      unsigned pg = OURO_NIL;
+    }
+    granted = __shfl_sync(vmask, granted, gl_leader);
+    x = __shfl_sync(vmask, x, gl_leader);
+    if (holder) {
       /* start word: spread groups of different warps over the chunk's words */
       const unsigned seed = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 0x9E3779B1u ^ (x * 0x85EBCA6Bu) ^ it;
-      if (in_g) pg = claim_pages(h, x, jppc, granted, jg, jleader, jrank, seed >> 7);
-      if (in_g && pg != OURO_NIL) {
+      const unsigned pg = claim_pages(h, x, ppc, granted, gmask, leader, rank, seed >> 7);
+      if (pg != OURO_NIL) {
         st = 1;
         page = pg;
         chunk = x;
