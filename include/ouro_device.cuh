@@ -392,8 +392,9 @@ __device__ inline unsigned spare_pop(const ouro_heap_dev &h, int c) {
   return OURO_NIL;
 }
 
-/* Set chunk x up as segment idx: every slot reads empty for its own position. */
-__device__ inline void seg_init(const ouro_heap_dev &h, unsigned x, unsigned idx, bool fresh) {
+/* Set chunk x up as segment idx, linked to next (OURO_NIL: none yet): every
+ * slot reads empty for its own position.  No fence: the caller publishes. */
+__device__ inline void seg_setup(const ouro_heap_dev &h, unsigned x, unsigned idx, bool fresh, unsigned next) {
   ouro_seg *s = seg_of(h, x);
   s->done = 0;
   /* A segment recycled from the spare stack always serves a higher index, so
@@ -415,7 +416,12 @@ __device__ inline void seg_init(const ouro_heap_dev &h, unsigned x, unsigned idx
       *reinterpret_cast<ulonglong2 *>(cells + i) = v;   /* seg_cap is even, cells 16-B aligned */
     }
   }
-  s->link = pack(idx, OURO_NIL);
+  s->link = pack(idx, next);
+}
+
+/* Set chunk x up as segment idx with no successor, and fence. */
+__device__ inline void seg_init(const ouro_heap_dev &h, unsigned x, unsigned idx, bool fresh) {
+  seg_setup(h, x, idx, fresh, OURO_NIL);
   __threadfence();
 }
 
@@ -436,16 +442,17 @@ __device__ inline unsigned seg_new(const ouro_heap_dev &h, int c, unsigned idx) 
   return x;
 }
 
-/* A retired list segment x is appended behind the back segment (ahead of
- * the producers, at most OURO_AHEAD_POS positions past the tail), so that
- * producers find their segments linked; else it joins the spare stack.
- * Appends are serial (each needs the previous link), so when many segments
- * retire at once most of them land on the spare stack: the thread that
- * wins an append keeps appending from the spare stack behind its own
- * segment while no other thread is appending. */
-__device__ inline void vl_recycle(const ouro_heap_dev &h, int c, unsigned x) {
+/* Retired list segments xs[0..k), in list order, are appended behind the
+ * back segment as one chain -- indices back + 1 .. back + k, each linked to
+ * the next, published by one store of the back's link -- at most up to
+ * OURO_AHEAD_POS positions past the tail, so that producers find their
+ * segments linked; what does not fit joins the spare stack.  A burst that
+ * retires many segments thus re-links them in runs rather than one append
+ * (a claim, a set-up and a publish of the back's link) per segment. */
+__device__ inline void vl_append_run(const ouro_heap_dev &h, int c, const unsigned *xs, unsigned k) {
   ouro_qhdr *q = qh(h, c);
-  for (int k = 0; k < 8 && x != OURO_NIL; ++k) {
+  unsigned placed = 0, ns = h.backoff_min_ns;
+  for (int tries = 0; tries < 16 && placed < k; ++tries) {
     const unsigned long long b = ld_acq(&q->back.v);
     const unsigned bx = lo32(b);
     if (bx >= OURO_BUSY) break;
@@ -456,35 +463,62 @@ __device__ inline void vl_recycle(const ouro_heap_dev &h, int c, unsigned x) {
       cas_ar(&q->back.v, b, pack(hi32(b) + 1, lo32(link)));
       continue;
     }
-    if (lo32(link) == OURO_BUSY) break;                  /* another thread is appending */
-    if ((unsigned long long)hi32(b) * h.seg_cap > ld_rlx(&q->tail.v) + OURO_AHEAD_POS) break;
+    if (lo32(link) == OURO_BUSY) {                       /* another thread is appending: its run is short */
+      backoff_wait(h, ns);
+      ns = min(ns * 2, h.backoff_max_ns);
+      continue;
+    }
+    const unsigned long long lim = ld_rlx(&q->tail.v) + OURO_AHEAD_POS;
+    const unsigned long long at = (unsigned long long)(hi32(b) + 1) * h.seg_cap;   /* first position appended */
+    if (at > lim) break;
+    const unsigned m = (unsigned)min((unsigned long long)(k - placed), (lim - at) / h.seg_cap + 1);
     if (cas_ar(&sg->link, link, pack(hi32(b), OURO_BUSY)) != link) continue;
-    seg_init(h, x, hi32(b) + 1, false);
-    st_rel(&sg->link, pack(hi32(b), x));
-    cas_ar(&q->back.v, b, pack(hi32(b) + 1, x));
-    st_rlx(&q->hint[(hi32(b) + 1) & (OURO_VL_HINTS - 1)], pack(hi32(b) + 1, x));
-    x = (lo32(ld_rlx(&q->spare.v)) != OURO_NIL) ? spare_pop(h, c) : OURO_NIL;   /* go on with a spare */
-    k = -1;
+    for (unsigned j = 0; j < m; ++j)
+      seg_setup(h, xs[placed + j], hi32(b) + 1 + j, false, j + 1 < m ? xs[placed + j + 1] : OURO_NIL);
+    __threadfence();
+    st_rel(&sg->link, pack(hi32(b), xs[placed]));
+    atomicMax(&q->back.v, pack(hi32(b) + m, xs[placed + m - 1]));   /* indices only grow */
+    for (unsigned j = 0; j < m; ++j)
+      st_rlx(&q->hint[(hi32(b) + 1 + j) & (OURO_VL_HINTS - 1)], pack(hi32(b) + 1 + j, xs[placed + j]));
+    placed += m;
   }
-  if (x != OURO_NIL) spare_push(h, c, x);
+  for (unsigned j = placed; j < k; ++j) spare_push(h, c, xs[j]);
 }
 
+#define OURO_VL_RUN 16   /* front segments one retire takes off the list at once */
+
 /* Retire fully used front segments (all slots produced and consumed, and a
- * successor linked): each is recycled behind the back (or spared). */
-__device__ inline void vl_advance(const ouro_heap_dev &h, int c) {
+ * successor linked): up to OURO_VL_RUN consecutive ones leave the list with
+ * one move of the front and are appended behind the back as a chain (or
+ * spared).  Out of line: it runs once per segment's worth of positions. */
+static __device__ __noinline__ void vl_advance(const ouro_heap_dev &h, int c) {
   ouro_qhdr *q = qh(h, c);
+  unsigned xs[OURO_VL_RUN];
   for (int i = 0; i < 64; ++i) {
-    unsigned long long f = ld_acq(&q->front.v);
-    unsigned fx = lo32(f);
-    if (fx >= OURO_BUSY) return;
-    unsigned long long link = ld_acq(&seg_of(h, fx)->link);
-    if (hi32(link) != hi32(f)) continue;
-    unsigned nxt = lo32(link);
-    if (nxt >= OURO_BUSY) return;
-    if (ld_acq32(&seg_of(h, fx)->done) != 2u * h.seg_cap) return;
-    unsigned long long nf = pack(hi32(f) + 1, nxt);
-    cas_ar(&q->back.v, f, nf);           /* never leave the back hint on a retired segment */
-    if (cas_ar(&q->front.v, f, nf) == f) vl_recycle(h, c, fx);
+    const unsigned long long f = ld_acq(&q->front.v);
+    if (lo32(f) >= OURO_BUSY) return;
+    unsigned k = 0;
+    bool stale = false;
+    unsigned long long cur = f;
+    while (k < OURO_VL_RUN) {
+      const unsigned cx = lo32(cur);
+      const unsigned long long link = ld_acq(&seg_of(h, cx)->link);
+      if (hi32(link) != hi32(cur)) {                     /* the front moved on meanwhile */
+        stale = k == 0;
+        break;
+      }
+      if (lo32(link) >= OURO_BUSY) break;
+      if (ld_acq32(&seg_of(h, cx)->done) != 2u * h.seg_cap) break;
+      xs[k++] = cx;
+      cur = pack(hi32(cur) + 1, lo32(link));
+    }
+    if (stale) continue;
+    if (!k) return;
+    const unsigned long long b = ld_acq(&q->back.v);   /* never leave the back hint on a retired segment */
+    if (lo32(b) < OURO_BUSY && hi32(b) < hi32(cur)) cas_ar(&q->back.v, b, cur);
+    if (cas_ar(&q->front.v, f, cur) != f) continue;
+    vl_append_run(h, c, xs, k);
+    if (k < OURO_VL_RUN) return;
   }
 }
 
