@@ -89,6 +89,7 @@ struct ouro_qhdr {
   ouro_line front;   /* virtualized list: oldest live segment (idx << 32 | chunk) */
   ouro_line back;    /* virtualized list: newest segment (hint) */
   ouro_line spare;   /* virtualized list: retired segments (tag << 32 | chunk) */
+  ouro_line adv;     /* virtualized list: 1 while one thread or warp retires front segments */
   unsigned long long hint[OURO_VL_HINTS];  /* virtualized list: segment lookaside */
 };
 
@@ -140,6 +141,11 @@ __device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long *p
 __device__ __forceinline__ unsigned ld_acq32(const unsigned *p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_rlx32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void st_rlx(unsigned long long *p, unsigned long long v) {
@@ -490,7 +496,9 @@ __device__ inline void vl_append_run(const ouro_heap_dev &h, int c, const unsign
 /* Retire fully used front segments (all slots produced and consumed, and a
  * successor linked): up to OURO_VL_RUN consecutive ones leave the list with
  * one move of the front and are appended behind the back as a chain (or
- * spared).  Out of line: it runs once per segment's worth of positions. */
+ * spared).  The single-lane form, for callers that are not a whole warp;
+ * several may race, the front moves by compare-and-swap.  Out of line: it
+ * runs once per segment's worth of positions. */
 static __device__ __noinline__ void vl_advance(const ouro_heap_dev &h, int c) {
   ouro_qhdr *q = qh(h, c);
   unsigned xs[OURO_VL_RUN];
@@ -519,6 +527,292 @@ static __device__ __noinline__ void vl_advance(const ouro_heap_dev &h, int c) {
     if (cas_ar(&q->front.v, f, cur) != f) continue;
     vl_append_run(h, c, xs, k);
     if (k < OURO_VL_RUN) return;
+  }
+}
+
+/* Is the front segment of the list fully used (its own index in its link,
+ * a successor linked, every position produced and consumed)? */
+__device__ inline bool vl_front_ready(const ouro_heap_dev &h, ouro_qhdr *q) {
+  const unsigned long long f = ld_acq(&q->front.v);
+  if (lo32(f) >= OURO_BUSY) return false;
+  const unsigned long long link = ld_acq(&seg_of(h, lo32(f))->link);
+  return hi32(link) == hi32(f) && lo32(link) < OURO_BUSY && ld_acq32(&seg_of(h, lo32(f))->done) == 2u * h.seg_cap;
+}
+
+#define OURO_VL_WIDE 2   /* front segments per lane in one round of the warp-wide retire */
+
+/* Value v[j / 32] of lane j % 32 (0 <= j < 32 * OURO_VL_WIDE); every lane
+ * of the warp calls. */
+__device__ __forceinline__ unsigned vl_pick(const unsigned (&v)[OURO_VL_WIDE], unsigned j) {
+  unsigned r = 0;
+#pragma unroll
+  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    const unsigned t = __shfl_sync(0xffffffffu, v[p], j & 31);
+    if ((j >> 5) == (unsigned)p) r = t;
+  }
+  return r;
+}
+
+/* The back hint of class c trails the list (segments were linked behind
+ * it by producers): every lane of the warp reads the segments of indices
+ * back + 1 .. back + 32 * OURO_VL_WIDE at once (lookaside hints, then
+ * links), and the hint moves to the last one of the leading run that is
+ * linked in order.  succ: the successor the back segment links to. */
+static __device__ __noinline__ void vl_back_chase_warp(const ouro_heap_dev &h, ouro_qhdr *q, unsigned long long b,
+                                                       unsigned succ) {
+  const unsigned lane = laneid(), bi = hi32(b);
+  unsigned xc[OURO_VL_WIDE], nxt[OURO_VL_WIDE];
+  unsigned long long lk[OURO_VL_WIDE];
+#pragma unroll
+  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    const unsigned j = 32u * p + lane;
+    if (j == 0) {
+      xc[p] = succ;
+    } else {
+      const unsigned long long e = ld_rlx(&q->hint[(bi + 1 + j) & (OURO_VL_HINTS - 1)]);
+      xc[p] = hi32(e) == bi + 1 + j && lo32(e) < OURO_BUSY ? lo32(e) : OURO_NIL;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < OURO_VL_WIDE; ++p) lk[p] = xc[p] != OURO_NIL ? ld_rlx(&seg_of(h, xc[p])->link) : 0ull;
+  fence_acq_rel();
+  unsigned run = 0;
+  bool stop = false;
+#pragma unroll
+  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    nxt[p] = lo32(lk[p]);
+    if (stop) continue;
+    const unsigned j = 32u * p + lane;
+    const unsigned carry = p ? __shfl_sync(0xffffffffu, nxt[p ? p - 1 : 0], 31) : succ;
+    const unsigned upn = __shfl_up_sync(0xffffffffu, nxt[p], 1);
+    const unsigned prev = lane == 0 ? carry : upn;
+    const bool linked = xc[p] != OURO_NIL && prev == xc[p] && hi32(lk[p]) == bi + 1 + j;
+    const unsigned vm = __ballot_sync(0xffffffffu, linked);
+    if (vm == 0xffffffffu) {
+      run += 32;
+      continue;
+    }
+    run += __ffs(~vm) - 1;
+    stop = true;
+  }
+  if (!run) return;   /* the successor is still being set up */
+  const unsigned xl = vl_pick(xc, run - 1);
+  if (lane == 0) atomicMax(&q->back.v, pack(bi + run, xl));   /* indices only grow */
+}
+
+/* vl_append_run for a whole warp: the run's chunks are held as x[p] by lane
+ * j % 32 for run offset j = 32 p + lane (j < k).  Lane 0 claims the back
+ * segment's empty link; every lane sets its own segments up; lane 0
+ * publishes the chain with one store; every lane then writes its segments'
+ * lookaside hints.  A back hint that trails the list is moved up to 128
+ * segments at a time; what finds no room goes to the spare stack as one
+ * chain (one push). */
+static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, int c,
+                                                       const unsigned (&x)[OURO_VL_WIDE], unsigned k) {
+  ouro_qhdr *q = qh(h, c);
+  const unsigned lane = laneid();
+  unsigned nx[OURO_VL_WIDE];   /* chunk at run offset j + 1 */
+#pragma unroll
+  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    const unsigned dn = __shfl_down_sync(0xffffffffu, x[p], 1);
+    const unsigned up = p + 1 < OURO_VL_WIDE ? __shfl_sync(0xffffffffu, x[p + 1 < OURO_VL_WIDE ? p + 1 : p], 0)
+                                             : OURO_NIL;
+    nx[p] = lane == 31 ? up : dn;
+  }
+  unsigned placed = 0, ns = h.backoff_min_ns;
+  for (int tries = 0; tries < 16 && placed < k; ++tries) {
+    unsigned long long b = 0, link = 0;
+    unsigned m = 0;
+    int act = 0;   /* 0: look again, 1: link claimed for m segments, 2: no room behind the back, 3: chase the back */
+    if (lane == 0) {
+      b = ld_acq(&q->back.v);
+      const unsigned bx = lo32(b);
+      if (bx >= OURO_BUSY) {
+        act = 2;
+      } else {
+        ouro_seg *sg = seg_of(h, bx);
+        link = ld_acq(&sg->link);
+        if (hi32(link) != hi32(b)) {                         /* stale back hint */
+        } else if (lo32(link) < OURO_BUSY) {                 /* a successor exists: the hint trails */
+          act = 3;
+        } else if (lo32(link) == OURO_BUSY) {                /* another thread is appending */
+          backoff_wait(h, ns);
+          ns = min(ns * 2, h.backoff_max_ns);
+        } else {
+          const unsigned long long lim = ld_rlx(&q->tail.v) + OURO_AHEAD_POS;
+          const unsigned long long at = (unsigned long long)(hi32(b) + 1) * h.seg_cap;
+          if (at > lim) {
+            act = 2;
+          } else {
+            m = (unsigned)min((unsigned long long)(k - placed), (lim - at) / h.seg_cap + 1);
+            if (cas_ar(&sg->link, link, pack(hi32(b), OURO_BUSY)) == link) act = 1;
+          }
+        }
+      }
+    }
+    act = __shfl_sync(0xffffffffu, act, 0);
+    if (act == 2) break;
+    if (act == 3) {
+      vl_back_chase_warp(h, q, __shfl_sync(0xffffffffu, b, 0), lo32(__shfl_sync(0xffffffffu, link, 0)));
+      continue;
+    }
+    if (act == 0) continue;
+    b = __shfl_sync(0xffffffffu, b, 0);
+    m = __shfl_sync(0xffffffffu, m, 0);
+    const unsigned bi = hi32(b);
+#pragma unroll
+    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+      const unsigned j = 32u * p + lane;
+      if (j >= placed && j < placed + m)
+        seg_setup(h, x[p], bi + 1 + (j - placed), false, j + 1 < placed + m ? nx[p] : OURO_NIL);
+    }
+    __threadfence();
+    const unsigned first = vl_pick(x, placed), last = vl_pick(x, placed + m - 1);
+    __syncwarp();
+    if (lane == 0) {
+      st_rel(&seg_of(h, lo32(b))->link, pack(bi, first));
+      atomicMax(&q->back.v, pack(bi + m, last));   /* indices only grow */
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+      const unsigned j = 32u * p + lane;
+      if (j >= placed && j < placed + m)
+        st_rlx(&q->hint[(bi + 1 + (j - placed)) & (OURO_VL_HINTS - 1)], pack(bi + 1 + (j - placed), x[p]));
+    }
+    placed += m;
+  }
+  if (placed < k) {   /* the rest onto the spare stack, as one chain */
+#pragma unroll
+    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+      const unsigned j = 32u * p + lane;
+      if (j >= placed && j + 1 < k) seg_of(h, x[p])->spare_next = nx[p];
+    }
+    __threadfence();
+    const unsigned first = vl_pick(x, placed), last = vl_pick(x, k - 1);
+    __syncwarp();
+    if (lane == 0) {
+      unsigned long long *top = &q->spare.v;
+      unsigned it = 0;
+      for (; it < h.spin_limit; ++it) {
+        const unsigned long long old = ld_acq(top);
+        seg_of(h, last)->spare_next = lo32(old);
+        __threadfence();
+        if (cas_ar(top, old, pack(hi32(old) + 1, first)) == old) break;
+      }
+      if (it == h.spin_limit) set_error(h, OURO_ERR_TIMEOUT, OURO_SITE_SPARE);
+    }
+    __syncwarp();
+  }
+}
+
+/* vl_advance for a whole warp (every lane calls).  One warp at a time
+ * retires (the class's adv lock): a warp that finds the lock taken returns,
+ * and the holder, once it let go, looks at the front once more, so that no
+ * retire is lost; retires thus gather into long runs and few appends
+ * instead of one short run (and one append behind the back) per caller.
+ * Lane j % 32 looks at the
+ * segment of index front + j for j < 32 * OURO_VL_WIDE: its chunk from the
+ * lookaside hint, its link and its done count, all loaded at once behind one
+ * fence, instead of following the links one dependent load at a time; the
+ * leading run of fully used segments leaves the list with one move of the
+ * front and is appended behind the back.  A segment whose hint is missing
+ * or stale ends the round; the next round starts at it (then the front). */
+static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h, int c);
+static __device__ __noinline__ void vl_advance_warp(const ouro_heap_dev &h, int c) {
+  ouro_qhdr *q = qh(h, c);
+  __syncwarp();   /* the lanes' done counts are ordered before the lock attempt */
+  for (int a = 0; a < 8; ++a) {
+    unsigned got = 0;
+    if (laneid() == 0) got = try_lock(&q->adv.v);
+    if (!__shfl_sync(0xffffffffu, got, 0)) return;
+    vl_advance_warp_runs(h, c);
+    unsigned again = 0;
+    if (laneid() == 0) {
+      unlock(&q->adv.v);
+      __threadfence();
+      again = vl_front_ready(h, q);
+    }
+    if (!__shfl_sync(0xffffffffu, again, 0)) return;
+  }
+}
+static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h, int c) {
+  ouro_qhdr *q = qh(h, c);
+  const unsigned lane = laneid(), used = 2u * h.seg_cap;
+  unsigned long long f = 0;
+  bool known = false;
+  for (int i = 0; i < 64; ++i) {
+    if (!known) {
+      if (lane == 0) f = ld_acq(&q->front.v);
+      f = __shfl_sync(0xffffffffu, f, 0);
+    }
+    known = false;
+    if (lo32(f) >= OURO_BUSY) return;
+    const unsigned fi = hi32(f);
+    unsigned x[OURO_VL_WIDE], nxt[OURO_VL_WIDE], dn[OURO_VL_WIDE];
+    unsigned long long lk[OURO_VL_WIDE];
+#pragma unroll
+    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+      const unsigned j = 32u * p + lane;
+      if (j == 0) {
+        x[p] = lo32(f);
+      } else {
+        const unsigned long long e = ld_rlx(&q->hint[(fi + j) & (OURO_VL_HINTS - 1)]);
+        x[p] = hi32(e) == fi + j && lo32(e) < OURO_BUSY ? lo32(e) : OURO_NIL;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+      lk[p] = 0;
+      dn[p] = 0;
+      if (x[p] != OURO_NIL) {
+        lk[p] = ld_rlx(&seg_of(h, x[p])->link);
+        dn[p] = ld_rlx32(&seg_of(h, x[p])->done);
+      }
+    }
+    fence_acq_rel();
+    /* offset j leaves if its chunk is the successor that offset j - 1 links
+     * to (offset 0: the front), its link carries index front + j and a
+     * successor, and all its positions were produced and consumed */
+    unsigned k = 0;
+    int stop = 0;   /* 1: a known segment is not done yet; 2: a segment not known from its hint */
+#pragma unroll
+    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+      nxt[p] = lo32(lk[p]);
+      if (stop) continue;
+      const unsigned j = 32u * p + lane;
+      const unsigned carry = p ? __shfl_sync(0xffffffffu, nxt[p ? p - 1 : 0], 31) : lo32(f);
+      const unsigned upn = __shfl_up_sync(0xffffffffu, nxt[p], 1);
+      const unsigned prev = lane == 0 ? carry : upn;
+      const bool known_j = x[p] != OURO_NIL && prev == x[p] && hi32(lk[p]) == fi + j;
+      const bool ready = known_j && nxt[p] < OURO_BUSY && dn[p] == used;
+      const unsigned rm = __ballot_sync(0xffffffffu, ready);
+      if (rm == 0xffffffffu) {
+        k += 32;
+        continue;
+      }
+      const unsigned jj = __ffs(~rm) - 1;
+      k += jj;
+      stop = (__ballot_sync(0xffffffffu, known_j) >> jj) & 1 ? 1 : 2;
+    }
+    if (k == 0) {
+      /* the front itself is not done, or it moved on meanwhile (its link
+       * holds another index): look again */
+      if (__shfl_sync(0xffffffffu, (unsigned)(hi32(lk[0]) != fi), 0)) continue;
+      return;
+    }
+    const unsigned long long cur = pack(fi + k, vl_pick(nxt, k - 1));
+    unsigned moved = 0;
+    if (lane == 0) {
+      const unsigned long long b = ld_acq(&q->back.v);   /* never leave the back hint on a retired segment */
+      if (lo32(b) < OURO_BUSY && hi32(b) < hi32(cur)) cas_ar(&q->back.v, b, cur);
+      moved = cas_ar(&q->front.v, f, cur) == f;
+    }
+    if (!__shfl_sync(0xffffffffu, moved, 0)) continue;
+    vl_append_run_warp(h, c, x, k);
+    if (stop == 1) return;
+    f = cur;   /* the next round starts at the new front */
+    known = true;
   }
 }
 
@@ -647,13 +941,25 @@ __device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsig
   const bool on = active && cell;
   const unsigned x = on ? (unsigned)(((const unsigned char *)cell - h.base) >> h.log2_chunk) : OURO_NIL;
   const unsigned g = warp_group(h, mask, x) & __ballot_sync(mask, on);
+  bool retire = false;
   if (on && laneid() == (unsigned)(__ffs(g) - 1)) {
     const unsigned n = __popc(g);
     const unsigned r = atomicAdd(&seg_of(h, x)->done, n) + n;
     if (r == 2u * h.seg_cap) {
       __threadfence();
-      if (QF == OURO_QF_LIST) vl_advance(h, c);
-      else va_retire(h, c, x);
+      if (QF != OURO_QF_LIST) va_retire(h, c, x);
+      else if (mask != 0xffffffffu) vl_advance(h, c);
+      else retire = true;
+    }
+  }
+  if (QF == OURO_QF_LIST && mask == 0xffffffffu) {
+    /* a whole warp: the front advance runs warp-wide, once per class that
+     * retired a segment */
+    unsigned rm = __ballot_sync(mask, retire);
+    while (rm) {
+      const int cj = __shfl_sync(mask, c, __ffs(rm) - 1);
+      rm &= ~__ballot_sync(mask, retire && c == cj);
+      vl_advance_warp(h, cj);
     }
   }
 }

@@ -435,6 +435,11 @@ namespace launch {
  * small batch still spreads over many blocks. */
 constexpr int BLK_WIDE = 4;
 inline bool blk_wide(size_t n) { return n >= (size_t)BLK_WIDE * 256 * ouro::host::sm_count(); }
+/* The plain-array batch free takes eight requests per thread in blocks of
+ * 128 once a batch fills every SM with four such blocks: a 2^20 batch then
+ * runs as one wave (1024 blocks, at most 56 registers a thread). */
+constexpr int FREE_WIDE = 8, FREE_BLOCK = 128;
+inline bool free_wide(size_t n) { return n >= (size_t)FREE_WIDE * FREE_BLOCK * 4 * ouro::host::sm_count(); }
 
 template <int V>
 ouro_status batch_malloc(ouro_heap *H, const uint32_t *d_sizes, void **d_ptrs, size_t n, cudaStream_t s) {
@@ -476,6 +481,12 @@ ouro_status batch_free(ouro_heap *H, void *const *d_ptrs, size_t n, cudaStream_t
   if constexpr (ouro_page_queues(V)) {
     if (!H->d.deopt) {
       if constexpr (ouro_qform(V) == OURO_QF_RING) {
+        if (free_wide(n)) {
+          k_batch_free_blk<V, FREE_WIDE>
+              <<<grid_for((n + FREE_WIDE - 1) / FREE_WIDE, FREE_BLOCK, 1 << 20), FREE_BLOCK, 0, s>>>(H->d, d_ptrs, n);
+          OURO_LAUNCHED();
+          return OURO_OK;
+        }
         if (blk_wide(n)) {
           k_batch_free_blk<V, BLK_WIDE><<<grid_for((n + BLK_WIDE - 1) / BLK_WIDE, block, 1 << 20), block, 0, s>>>(
               H->d, d_ptrs, n);

@@ -89,12 +89,14 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
 }
 #define OURO_GOLD 0x9E3779B9u
 
+/* per-lane check counters: mismatches and the XOR fold in 32 bits (the
+ * words are 32-bit), the sum and the word count in 64 */
 struct payload_acc {
-  unsigned long long mism = 0, x = 0, s = 0, words = 0;
+  unsigned mism = 0, x = 0;
+  unsigned long long s = 0, words = 0;
   __device__ void fold(uint32_t v) {
     x ^= v;
     s += v;
-    words++;
   }
 };
 
@@ -117,9 +119,8 @@ __device__ __forceinline__ uint4 pat4(uint32_t key, uint32_t w0) {
 
 __device__ __forceinline__ void check4(const uint4 &got, const uint4 &want, payload_acc &a) {
   a.mism += (got.x != want.x) + (got.y != want.y) + (got.z != want.z) + (got.w != want.w);
-  a.x ^= (unsigned long long)(got.x ^ got.y ^ got.z ^ got.w);
+  a.x ^= got.x ^ got.y ^ got.z ^ got.w;
   a.s += (unsigned long long)got.x + got.y + got.z + got.w;
-  a.words += 4;
 }
 
 /* words [4*units, nw) and the tail bytes of one block: one lane */
@@ -163,6 +164,7 @@ __device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint
         uint32_t v = __ldcg(reinterpret_cast<const uint32_t *>(p));
         a.mism += v != tid;
         a.fold(v);
+        a.words++;
       }
     }
     return;
@@ -195,7 +197,10 @@ __device__ void warp_payload(unsigned char *p, uint32_t size, uint32_t tid, uint
         check4(g3, pat4(bkey, 4 * (u + 96)), a);
       }
       for (; u < units; u += 32) check4(__ldcg(u4 + u), pat4(bkey, 4 * u), a);
-      if (lane == (OP == PAY_FUSED ? (rest_lane + 31) & 31 : rest_lane)) block_rest<false>(bp, bkey, nw, tail, a);
+      if (lane == (OP == PAY_FUSED ? (rest_lane + 31) & 31 : rest_lane)) {
+        block_rest<false>(bp, bkey, nw, tail, a);
+        a.words += nw + (tail != 0);
+      }
     }
   }
 }
@@ -205,8 +210,9 @@ __device__ inline void flush_acc(payload_acc &a, unsigned long long nulls, ouro_
   __shared__ unsigned long long sm[5];
   if (threadIdx.x < 5) sm[threadIdx.x] = 0;
   __syncthreads();
+  unsigned long long mism = a.mism;   /* per lane 32 bits; summed over the warp in 64 */
   for (int o = 16; o; o >>= 1) {
-    a.mism += __shfl_xor_sync(0xffffffffu, a.mism, o);
+    mism += __shfl_xor_sync(0xffffffffu, mism, o);
     a.x ^= __shfl_xor_sync(0xffffffffu, a.x, o);
     a.s += __shfl_xor_sync(0xffffffffu, a.s, o);
     a.words += __shfl_xor_sync(0xffffffffu, a.words, o);
@@ -214,8 +220,8 @@ __device__ inline void flush_acc(payload_acc &a, unsigned long long nulls, ouro_
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&sm[0], nulls);
-    atomicAdd(&sm[1], a.mism);
-    atomicXor(&sm[2], a.x);
+    atomicAdd(&sm[1], mism);
+    atomicXor(&sm[2], (unsigned long long)a.x);
     atomicAdd(&sm[3], a.s);
     atomicAdd(&sm[4], a.words);
   }
@@ -232,8 +238,9 @@ __device__ inline void flush_acc(payload_acc &a, unsigned long long nulls, ouro_
 
 /* warp reduction of the check counters; lane 0 adds them to *out */
 __device__ inline void warp_flush(payload_acc &a, unsigned long long nulls, ouro_check *out) {
+  unsigned long long mism = a.mism;   /* per lane 32 bits; summed over the warp in 64 */
   for (int o = 16; o; o >>= 1) {
-    a.mism += __shfl_xor_sync(0xffffffffu, a.mism, o);
+    mism += __shfl_xor_sync(0xffffffffu, mism, o);
     a.x ^= __shfl_xor_sync(0xffffffffu, a.x, o);
     a.s += __shfl_xor_sync(0xffffffffu, a.s, o);
     a.words += __shfl_xor_sync(0xffffffffu, a.words, o);
@@ -241,8 +248,8 @@ __device__ inline void warp_flush(payload_acc &a, unsigned long long nulls, ouro
   }
   if ((threadIdx.x & 31) == 0) {
     if (nulls) atomicAdd(&out->nulls, nulls);
-    if (a.mism) atomicAdd(&out->mismatches, a.mism);
-    atomicXor(&out->xor64, a.x);
+    if (mism) atomicAdd(&out->mismatches, mism);
+    atomicXor(&out->xor64, (unsigned long long)a.x);
     atomicAdd(&out->sum64, a.s);
     atomicAdd(&out->words, a.words);
   }

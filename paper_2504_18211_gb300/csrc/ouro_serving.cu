@@ -114,14 +114,15 @@ __device__ void serve_block_payload(unsigned char *bp, uint32_t bytes, uint32_t 
   __syncwarp();
   payload_acc a;
   for (uint32_t u = (lane + 1) & 31; u < units; u += 32) check4(__ldcg(u4 + u), pat4(key, 4 * u), a);
+  unsigned long long m = a.mism;
   for (int o = 16; o; o >>= 1) {
     a.x ^= __shfl_xor_sync(0xffffffffu, a.x, o);
     a.s += __shfl_xor_sync(0xffffffffu, a.s, o);
-    a.mism += __shfl_xor_sync(0xffffffffu, a.mism, o);
+    m += __shfl_xor_sync(0xffffffffu, m, o);
   }
   x = a.x;
   s = a.s;
-  mism = a.mism;
+  mism = m;
 }
 
 /* ---------------------------------------------------------------- phases
