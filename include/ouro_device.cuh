@@ -2464,43 +2464,47 @@ __device__ void ouro_block_begin(ouro_block_ctx<WARPS> &ctx) {
 }
 
 /* Every thread of the block calls: each warp returns its staged pages to
- * the class queues, then __syncthreads. */
+ * the class queues (page queues) or to their chunks (chunk queues), then
+ * __syncthreads.  The staged ids of all classes go back 32 at a time, lane j
+ * of a round taking the j-th id of the round in class order, so that one
+ * call serves the lanes of several classes at once (the classes' queue
+ * atomics in flight together) instead of one call per class. */
 template <int V, int WARPS>
 __device__ void ouro_block_end_v(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h) {
   using namespace ouro::detail;
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   __syncwarp();
-  if constexpr (ouro_page_queues(V)) {
-    for (unsigned c = 0; c < h.n_classes; ++c) {
-      const unsigned n = ctx.cnt[w][c];
-      if (!n) continue;
-      const bool mine = lane < n;
-      const unsigned m = __ballot_sync(0xffffffffu, mine);
-      if (mine) page_free<V>(h, (int)c, ctx.ids[w][c][lane], m);
-      __syncwarp();
-      if (lane == 0) {
-        ctx.cnt[w][c] = 0;
-        /* these pages were counted as freed when they were staged */
-        stat_add(h, c, OURO_ST_FREE, 0ull - (unsigned long long)n);
+  unsigned total = 0;
+  for (unsigned c = 0; c < h.n_classes; ++c) total += ctx.cnt[w][c];
+  for (unsigned j0 = 0; j0 < total; j0 += 32) {
+    const unsigned j = j0 + lane;
+    int cj = -1;
+    unsigned item = 0;
+    if (j < total) {
+      unsigned acc = 0;
+      for (unsigned c = 0; c < h.n_classes; ++c) {
+        const unsigned k = ctx.cnt[w][c];
+        if (j < acc + k) {
+          cj = (int)c;
+          item = ctx.ids[w][c][j - acc];
+          break;
+        }
+        acc += k;
       }
-      __syncwarp();
     }
-  } else {
-    /* chunk queues: the staged pages go back to their chunks (bits, counts,
-     * re-queued chunks), 32 lanes at a time */
-    for (unsigned c = 0; c < h.n_classes; ++c) {
-      const unsigned n = ctx.cnt[w][c];
-      if (!n) continue;
-      const bool mine = lane < n;
-      void *p = mine ? h.base + ((size_t)ctx.ids[w][c][lane] << (4 + c)) : nullptr;
-      chunk_free_impl<V>(h, mine ? (int)c : -1, p, 0xffffffffu);
-      __syncwarp();
-      if (lane == 0) {
-        ctx.cnt[w][c] = 0;
-        stat_add(h, c, OURO_ST_FREE, 0ull - (unsigned long long)n);
-      }
-      __syncwarp();
+    if constexpr (ouro_page_queues(V)) {
+      const unsigned m = __ballot_sync(0xffffffffu, cj >= 0);
+      if (cj >= 0) page_free<V>(h, cj, item, m);
+    } else {
+      void *p = cj >= 0 ? h.base + ((size_t)item << (4 + cj)) : nullptr;
+      chunk_free_impl<V>(h, cj, p, 0xffffffffu);
     }
+    __syncwarp();
+  }
+  if (lane < h.n_classes && ctx.cnt[w][lane]) {
+    /* these pages were counted as freed when they were staged */
+    stat_add(h, lane, OURO_ST_FREE, 0ull - (unsigned long long)ctx.cnt[w][lane]);
+    ctx.cnt[w][lane] = 0;
   }
   __syncthreads();
 }

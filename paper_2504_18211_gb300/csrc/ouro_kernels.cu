@@ -59,6 +59,12 @@ __global__ void __launch_bounds__(256, 4) k_batch_malloc_blk(ouro_heap_dev h, co
   constexpr bool RING = ouro_qform(V) == OURO_QF_RING;
   __shared__ unsigned s_cnt[OURO_MAX_CLASSES], s_ok[OURO_MAX_CLASSES];
   __shared__ unsigned long long s_pos[OURO_MAX_CLASSES];
+  __shared__ unsigned long long *s_ring[OURO_MAX_CLASSES];
+  __shared__ unsigned long long s_rmask[OURO_MAX_CLASSES];
+  if (threadIdx.x < OURO_MAX_CLASSES) {
+    s_ring[threadIdx.x] = h.cells + h.ring_off[threadIdx.x];
+    s_rmask[threadIdx.x] = h.ring_mask[threadIdx.x];
+  }
   const size_t span = (size_t)blockDim.x * R;
   for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
     uint32_t sz[R];
@@ -94,14 +100,14 @@ __global__ void __launch_bounds__(256, 4) k_batch_malloc_blk(ouro_heap_dev h, co
       unsigned long long v[R];
 #pragma unroll
       for (int r = 0; r < R; ++r)
-        v[r] = pend[r] && cls[r] < (int)h.n_classes ? ld_rlx(ring_slot(h, cls[r], pos[r])) : 0ull;
+        v[r] = pend[r] && cls[r] < (int)h.n_classes ? ld_rlx(s_ring[cls[r]] + (pos[r] & s_rmask[cls[r]])) : 0ull;
       fence_acq_rel();
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!pend[r] || cls[r] >= (int)h.n_classes) continue;
         const int d = slot_d(v[r], pos[r]);
         if (d == 1 || d == 2) {   /* an item, or the heap's null answer: take it, retire the slot */
-          st_rlx(ring_slot(h, cls[r], pos[r]), slot(pos[r] + h.ring_mask[cls[r]] + 1, 0));
+          st_rlx(s_ring[cls[r]] + (pos[r] & s_rmask[cls[r]]), slot(pos[r] + s_rmask[cls[r]] + 1, 0));
           if (d == 1) res[r] = h.base + ((size_t)lo32(v[r]) << (4 + cls[r]));
           pend[r] = false;
         }
@@ -133,6 +139,12 @@ __global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *c
   constexpr bool RING = ouro_qform(V) == OURO_QF_RING;
   __shared__ unsigned s_cnt[OURO_MAX_CLASSES];
   __shared__ unsigned long long s_pos[OURO_MAX_CLASSES];
+  __shared__ unsigned long long *s_ring[OURO_MAX_CLASSES];
+  __shared__ unsigned long long s_rmask[OURO_MAX_CLASSES];
+  if (threadIdx.x < OURO_MAX_CLASSES) {
+    s_ring[threadIdx.x] = h.cells + h.ring_off[threadIdx.x];
+    s_rmask[threadIdx.x] = h.ring_mask[threadIdx.x];
+  }
   const size_t span = (size_t)blockDim.x * R;
   for (size_t base = (size_t)blockIdx.x * span; base < n; base += (size_t)gridDim.x * span) {
     void *p[R];
@@ -169,7 +181,8 @@ __global__ void __launch_bounds__(256) k_batch_free_blk(ouro_heap_dev h, void *c
       fence_acq_rel();
 #pragma unroll
       for (int r = 0; r < R; ++r)
-        old[r] = pend[r] ? cas_rlx(ring_slot(h, cls[r], pos[r]), slot(pos[r], 0), slot(pos[r] + 1, item[r])) : 0ull;
+        old[r] = pend[r] ? cas_rlx(s_ring[cls[r]] + (pos[r] & s_rmask[cls[r]]), slot(pos[r], 0), slot(pos[r] + 1, item[r]))
+                         : 0ull;
 #pragma unroll
       for (int r = 0; r < R; ++r)
         if (pend[r] && old[r] == slot(pos[r], 0)) pend[r] = false;
