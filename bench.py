@@ -79,8 +79,8 @@ def dist_env():
 # from the sources whose digest is recorded; null once they change.
 FUSED_KERNEL_SOURCES = ("include/ouro_device.cuh", "paper_2504_18211_gb300/csrc/ouro_payload.cuh",
                         "paper_2504_18211_gb300/csrc/ouro_kernels.cu", "paper_2504_18211_gb300/csrc/ouro_internal.cuh")
-FUSED_TRAFFIC = {"sources_sha256": "a9e31112c0ae1ae898e99430b0e5acda50711e9d027f817ffcc6f31c559813e0",
-                 "bytes_per_launch": 1655597312}
+FUSED_TRAFFIC = {"sources_sha256": "f83a0cc67a485260a46a9b6fd4b4253964fbb5bf1b568b25dde74079ed42b24a",
+                 "bytes_per_launch": 1646689024}
 
 
 def kernel_sources_digest() -> str:
@@ -128,7 +128,16 @@ def workload_config(threads, variant, form="fused", heap_bytes=HEAP_BYTES, stagi
                         f"allocate / write pattern / read back + check / free, one round per step",
             "heap_bytes": heap_bytes, "chunk_bytes": CHUNK, "threads": threads, "variant": variant,
             "form": form, "staging": staging,
-            "l2": "inputs larger than L2: ~1.7 GB of payload per round (L2 129 MB)"}
+            "l2": l2_note(threads)}
+
+
+def l2_note(threads: int) -> str:
+    """How the round's payload compares with L2 (mean sweep block: the mean
+    of 2^k B over k in [4, 13], 1636.8 B)."""
+    gb = threads * 1636.8 / 1e9
+    if gb * 1e9 > 129e6:
+        return f"inputs larger than L2: ~{gb:.2f} GB of payload per round (L2 129 MB)"
+    return f"payload ~{gb * 1e3:.0f} MB per round, within L2 (129 MB): rounds are not HBM-bound"
 
 
 # ----------------------------------------------------------------- helpers
