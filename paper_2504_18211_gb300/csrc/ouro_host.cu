@@ -163,7 +163,7 @@ extern "C" ouro_status ouro_heap_create_ex(size_t bytes, size_t chunk_bytes, our
   d.backoff_max_ns = o.backoff_max_ns;
   d.max_carve = o.max_carve;
   d.checked = o.checked ? 1u : 0u;
-  d.staging = (o.staging && is_page(variant)) ? 1u : 0u;
+  d.staging = o.staging ? 1u : 0u;   /* every queue form */
   d.deopt = o.deopt ? 1u : 0u;
   d.pad = 0;
 
