@@ -608,7 +608,8 @@ static __device__ __noinline__ void vl_back_chase_warp(const ouro_heap_dev &h, o
  * segments at a time; what finds no room goes to the spare stack as one
  * chain (one push). */
 static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, int c,
-                                                       const unsigned (&x)[OURO_VL_WIDE], unsigned k) {
+                                                       const unsigned (&x)[OURO_VL_WIDE], unsigned k,
+                                                       unsigned long long &bk) {
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
   unsigned nx[OURO_VL_WIDE];   /* chunk at run offset j + 1 */
@@ -625,28 +626,33 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
     unsigned m = 0;
     int act = 0;   /* 0: look again, 1: link claimed for m segments, 2: no room behind the back, 3: chase the back */
     if (lane == 0) {
-      b = ld_acq(&q->back.v);
+      /* the first try starts from the back this warp published last (a
+       * segment whose link still has no successor is the list's last) */
+      b = tries == 0 && bk ? bk : ld_acq(&q->back.v);
       const unsigned bx = lo32(b);
       if (bx >= OURO_BUSY) {
         act = 2;
       } else {
         ouro_seg *sg = seg_of(h, bx);
-        link = ld_acq(&sg->link);
-        if (hi32(link) != hi32(b)) {                         /* stale back hint */
-        } else if (lo32(link) < OURO_BUSY) {                 /* a successor exists: the hint trails */
-          act = 3;
-        } else if (lo32(link) == OURO_BUSY) {                /* another thread is appending */
-          backoff_wait(h, ns);
-          ns = min(ns * 2, h.backoff_max_ns);
-        } else {
-          const unsigned long long lim = ld_rlx(&q->tail.v) + OURO_AHEAD_POS;
+        const unsigned long long tail = ld_rlx(&q->tail.v);
+        const unsigned long long empty = pack(hi32(b), OURO_NIL);
+        link = cas_ar(&sg->link, empty, pack(hi32(b), OURO_BUSY));   /* claim the empty link */
+        if (link == empty) {
+          const unsigned long long lim = tail + OURO_AHEAD_POS;
           const unsigned long long at = (unsigned long long)(hi32(b) + 1) * h.seg_cap;
           if (at > lim) {
+            st_rel(&sg->link, empty);
             act = 2;
           } else {
             m = (unsigned)min((unsigned long long)(k - placed), (lim - at) / h.seg_cap + 1);
-            if (cas_ar(&sg->link, link, pack(hi32(b), OURO_BUSY)) == link) act = 1;
+            act = 1;
           }
+        } else if (hi32(link) != hi32(b)) {                  /* stale back hint */
+        } else if (lo32(link) < OURO_BUSY) {                 /* a successor exists: the hint trails */
+          act = 3;
+        } else {                                             /* another thread is appending */
+          backoff_wait(h, ns);
+          ns = min(ns * 2, h.backoff_max_ns);
         }
       }
     }
@@ -673,6 +679,7 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
       st_rel(&seg_of(h, lo32(b))->link, pack(bi, first));
       atomicMax(&q->back.v, pack(bi + m, last));   /* indices only grow */
     }
+    bk = pack(bi + m, last);
     __syncwarp();
 #pragma unroll
     for (int p = 0; p < OURO_VL_WIDE; ++p) {
@@ -739,7 +746,7 @@ static __device__ __noinline__ void vl_advance_warp(const ouro_heap_dev &h, int 
 static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h, int c) {
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid(), used = 2u * h.seg_cap;
-  unsigned long long f = 0;
+  unsigned long long f = 0, bk = 0;   /* bk: the back this warp published last, 0 none */
   bool known = false;
   for (int i = 0; i < 64; ++i) {
     if (!known) {
@@ -804,12 +811,16 @@ static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h,
     const unsigned long long cur = pack(fi + k, vl_pick(nxt, k - 1));
     unsigned moved = 0;
     if (lane == 0) {
-      const unsigned long long b = ld_acq(&q->back.v);   /* never leave the back hint on a retired segment */
-      if (lo32(b) < OURO_BUSY && hi32(b) < hi32(cur)) cas_ar(&q->back.v, b, cur);
+      /* never leave the back hint on a retired segment (the hint only
+       * grows: a back this warp published at or past cur needs no look) */
+      if (!bk || hi32(bk) < hi32(cur)) {
+        const unsigned long long b = ld_acq(&q->back.v);
+        if (lo32(b) < OURO_BUSY && hi32(b) < hi32(cur)) cas_ar(&q->back.v, b, cur);
+      }
       moved = cas_ar(&q->front.v, f, cur) == f;
     }
     if (!__shfl_sync(0xffffffffu, moved, 0)) continue;
-    vl_append_run_warp(h, c, x, k);
+    vl_append_run_warp(h, c, x, k, bk);
     if (stop == 1) return;
     f = cur;   /* the next round starts at the new front */
     known = true;
