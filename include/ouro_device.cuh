@@ -539,14 +539,20 @@ __device__ inline bool vl_front_ready(const ouro_heap_dev &h, ouro_qhdr *q) {
   return hi32(link) == hi32(f) && lo32(link) < OURO_BUSY && ld_acq32(&seg_of(h, lo32(f))->done) == 2u * h.seg_cap;
 }
 
-#define OURO_VL_WIDE 2   /* front segments per lane in one round of the warp-wide retire */
+/* Front segments per lane in one round of the warp-wide retire (W below):
+ * two for most callers; four for the block-aggregated batch kernels,
+ * which run long single-class bursts (more registers in the walk, which
+ * other kernels would carry too). */
+#define OURO_VL_WIDE 2
+#define OURO_VL_WIDE_BATCH 4
 
-/* Value v[j / 32] of lane j % 32 (0 <= j < 32 * OURO_VL_WIDE); every lane
+/* Value v[j / 32] of lane j % 32 (0 <= j < 32 * W); every lane
  * of the warp calls. */
-__device__ __forceinline__ unsigned vl_pick(const unsigned (&v)[OURO_VL_WIDE], unsigned j) {
+template <int W>
+__device__ __forceinline__ unsigned vl_pick(const unsigned (&v)[W], unsigned j) {
   unsigned r = 0;
 #pragma unroll
-  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+  for (int p = 0; p < W; ++p) {
     const unsigned t = __shfl_sync(0xffffffffu, v[p], j & 31);
     if ((j >> 5) == (unsigned)p) r = t;
   }
@@ -555,16 +561,17 @@ __device__ __forceinline__ unsigned vl_pick(const unsigned (&v)[OURO_VL_WIDE], u
 
 /* The back hint of class c trails the list (segments were linked behind
  * it by producers): every lane of the warp reads the segments of indices
- * back + 1 .. back + 32 * OURO_VL_WIDE at once (lookaside hints, then
+ * back + 1 .. back + 32 * W at once (lookaside hints, then
  * links), and the hint moves to the last one of the leading run that is
  * linked in order.  succ: the successor the back segment links to. */
+template <int W>
 static __device__ __noinline__ void vl_back_chase_warp(const ouro_heap_dev &h, ouro_qhdr *q, unsigned long long b,
                                                        unsigned succ) {
   const unsigned lane = laneid(), bi = hi32(b);
-  unsigned xc[OURO_VL_WIDE], nxt[OURO_VL_WIDE];
-  unsigned long long lk[OURO_VL_WIDE];
+  unsigned xc[W], nxt[W];
+  unsigned long long lk[W];
 #pragma unroll
-  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+  for (int p = 0; p < W; ++p) {
     const unsigned j = 32u * p + lane;
     if (j == 0) {
       xc[p] = succ;
@@ -574,12 +581,12 @@ static __device__ __noinline__ void vl_back_chase_warp(const ouro_heap_dev &h, o
     }
   }
 #pragma unroll
-  for (int p = 0; p < OURO_VL_WIDE; ++p) lk[p] = xc[p] != OURO_NIL ? ld_rlx(&seg_of(h, xc[p])->link) : 0ull;
+  for (int p = 0; p < W; ++p) lk[p] = xc[p] != OURO_NIL ? ld_rlx(&seg_of(h, xc[p])->link) : 0ull;
   fence_acq_rel();
   unsigned run = 0;
   bool stop = false;
 #pragma unroll
-  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+  for (int p = 0; p < W; ++p) {
     nxt[p] = lo32(lk[p]);
     if (stop) continue;
     const unsigned j = 32u * p + lane;
@@ -607,16 +614,17 @@ static __device__ __noinline__ void vl_back_chase_warp(const ouro_heap_dev &h, o
  * lookaside hints.  A back hint that trails the list is moved up to 128
  * segments at a time; what finds no room goes to the spare stack as one
  * chain (one push). */
+template <int W>
 static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, int c,
-                                                       const unsigned (&x)[OURO_VL_WIDE], unsigned k,
+                                                       const unsigned (&x)[W], unsigned k,
                                                        unsigned long long &bk) {
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid();
-  unsigned nx[OURO_VL_WIDE];   /* chunk at run offset j + 1 */
+  unsigned nx[W];   /* chunk at run offset j + 1 */
 #pragma unroll
-  for (int p = 0; p < OURO_VL_WIDE; ++p) {
+  for (int p = 0; p < W; ++p) {
     const unsigned dn = __shfl_down_sync(0xffffffffu, x[p], 1);
-    const unsigned up = p + 1 < OURO_VL_WIDE ? __shfl_sync(0xffffffffu, x[p + 1 < OURO_VL_WIDE ? p + 1 : p], 0)
+    const unsigned up = p + 1 < W ? __shfl_sync(0xffffffffu, x[p + 1 < W ? p + 1 : p], 0)
                                              : OURO_NIL;
     nx[p] = lane == 31 ? up : dn;
   }
@@ -659,7 +667,7 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
     act = __shfl_sync(0xffffffffu, act, 0);
     if (act == 2) break;
     if (act == 3) {
-      vl_back_chase_warp(h, q, __shfl_sync(0xffffffffu, b, 0), lo32(__shfl_sync(0xffffffffu, link, 0)));
+      vl_back_chase_warp<W>(h, q, __shfl_sync(0xffffffffu, b, 0), lo32(__shfl_sync(0xffffffffu, link, 0)));
       continue;
     }
     if (act == 0) continue;
@@ -667,7 +675,7 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
     m = __shfl_sync(0xffffffffu, m, 0);
     const unsigned bi = hi32(b);
 #pragma unroll
-    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    for (int p = 0; p < W; ++p) {
       const unsigned j = 32u * p + lane;
       if (j >= placed && j < placed + m)
         seg_setup(h, x[p], bi + 1 + (j - placed), false, j + 1 < placed + m ? nx[p] : OURO_NIL);
@@ -682,7 +690,7 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
     bk = pack(bi + m, last);
     __syncwarp();
 #pragma unroll
-    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    for (int p = 0; p < W; ++p) {
       const unsigned j = 32u * p + lane;
       if (j >= placed && j < placed + m)
         st_rlx(&q->hint[(bi + 1 + (j - placed)) & (OURO_VL_HINTS - 1)], pack(bi + 1 + (j - placed), x[p]));
@@ -691,7 +699,7 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
   }
   if (placed < k) {   /* the rest onto the spare stack, as one chain */
 #pragma unroll
-    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    for (int p = 0; p < W; ++p) {
       const unsigned j = 32u * p + lane;
       if (j >= placed && j + 1 < k) seg_of(h, x[p])->spare_next = nx[p];
     }
@@ -719,13 +727,15 @@ static __device__ __noinline__ void vl_append_run_warp(const ouro_heap_dev &h, i
  * retire is lost; retires thus gather into long runs and few appends
  * instead of one short run (and one append behind the back) per caller.
  * Lane j % 32 looks at the
- * segment of index front + j for j < 32 * OURO_VL_WIDE: its chunk from the
+ * segment of index front + j for j < 32 * W: its chunk from the
  * lookaside hint, its link and its done count, all loaded at once behind one
  * fence, instead of following the links one dependent load at a time; the
  * leading run of fully used segments leaves the list with one move of the
  * front and is appended behind the back.  A segment whose hint is missing
  * or stale ends the round; the next round starts at it (then the front). */
+template <int W>
 static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h, int c);
+template <int W>
 static __device__ __noinline__ void vl_advance_warp(const ouro_heap_dev &h, int c) {
   ouro_qhdr *q = qh(h, c);
   __syncwarp();   /* the lanes' done counts are ordered before the lock attempt */
@@ -733,7 +743,7 @@ static __device__ __noinline__ void vl_advance_warp(const ouro_heap_dev &h, int 
     unsigned got = 0;
     if (laneid() == 0) got = try_lock(&q->adv.v);
     if (!__shfl_sync(0xffffffffu, got, 0)) return;
-    vl_advance_warp_runs(h, c);
+    vl_advance_warp_runs<W>(h, c);
     unsigned again = 0;
     if (laneid() == 0) {
       unlock(&q->adv.v);
@@ -743,6 +753,7 @@ static __device__ __noinline__ void vl_advance_warp(const ouro_heap_dev &h, int 
     if (!__shfl_sync(0xffffffffu, again, 0)) return;
   }
 }
+template <int W>
 static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h, int c) {
   ouro_qhdr *q = qh(h, c);
   const unsigned lane = laneid(), used = 2u * h.seg_cap;
@@ -756,10 +767,10 @@ static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h,
     known = false;
     if (lo32(f) >= OURO_BUSY) return;
     const unsigned fi = hi32(f);
-    unsigned x[OURO_VL_WIDE], nxt[OURO_VL_WIDE], dn[OURO_VL_WIDE];
-    unsigned long long lk[OURO_VL_WIDE];
+    unsigned x[W], nxt[W], dn[W];
+    unsigned long long lk[W];
 #pragma unroll
-    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    for (int p = 0; p < W; ++p) {
       const unsigned j = 32u * p + lane;
       if (j == 0) {
         x[p] = lo32(f);
@@ -769,7 +780,7 @@ static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h,
       }
     }
 #pragma unroll
-    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    for (int p = 0; p < W; ++p) {
       lk[p] = 0;
       dn[p] = 0;
       if (x[p] != OURO_NIL) {
@@ -784,7 +795,7 @@ static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h,
     unsigned k = 0;
     int stop = 0;   /* 1: a known segment is not done yet; 2: a segment not known from its hint */
 #pragma unroll
-    for (int p = 0; p < OURO_VL_WIDE; ++p) {
+    for (int p = 0; p < W; ++p) {
       nxt[p] = lo32(lk[p]);
       if (stop) continue;
       const unsigned j = 32u * p + lane;
@@ -820,7 +831,7 @@ static __device__ __noinline__ void vl_advance_warp_runs(const ouro_heap_dev &h,
       moved = cas_ar(&q->front.v, f, cur) == f;
     }
     if (!__shfl_sync(0xffffffffu, moved, 0)) continue;
-    vl_append_run_warp(h, c, x, k, bk);
+    vl_append_run_warp<W>(h, c, x, k, bk);
     if (stop == 1) return;
     f = cur;   /* the next round starts at the new front */
     known = true;
@@ -946,7 +957,7 @@ __device__ inline void seg_event(const ouro_heap_dev &h, int c, const unsigned l
 /* Position events of the lanes of mask (every lane of mask calls): lanes
  * with `active` and a slot count one event on the segment of their slot;
  * lanes on the same segment are summed into one atomic. */
-template <int QF>
+template <int QF, int W = OURO_VL_WIDE>
 __device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsigned long long *cell, bool active,
                                       unsigned mask) {
   const bool on = active && cell;
@@ -970,7 +981,7 @@ __device__ inline void seg_event_warp(const ouro_heap_dev &h, int c, const unsig
     while (rm) {
       const int cj = __shfl_sync(mask, c, __ffs(rm) - 1);
       rm &= ~__ballot_sync(mask, retire && c == cj);
-      vl_advance_warp(h, cj);
+      vl_advance_warp<W>(h, cj);
     }
   }
 }
@@ -1521,7 +1532,7 @@ __device__ void *page_malloc(const ouro_heap_dev &h, int cls, unsigned vmask, un
       }
     }
   }
-  if (VL) seg_event_warp<QF>(h, cls, cell, st != 0 && (st != 3 || gave_up), vmask);
+  if (VL) seg_event_warp<QF, RESERVED ? OURO_VL_WIDE_BATCH : OURO_VL_WIDE>(h, cls, cell, st != 0 && (st != 3 || gave_up), vmask);
 
   void *res = nullptr;
   if (st == 1) {
