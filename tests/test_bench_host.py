@@ -85,3 +85,14 @@ def test_workload_config_names_the_workload():
     assert c["threads"] == bench.THREADS and c["variant"] == "page_array"
     assert "size sweep" in c["workload"] and "L2" in c["l2"]
     assert not {"model", "global_batch", "seq_len"} & set(c)
+
+
+def test_l2_note_follows_the_payload():
+    """The config's L2 statement is computed from the workload: the
+    headline's ~1.7 GB of payload is larger than L2, a small batch is not."""
+    from paper_2504_18211_gb300 import workloads as W
+    big = bench.l2_note(bench.THREADS)
+    assert big.startswith("inputs larger than L2") and "1.72 GB" in big
+    mean = float(W.sweep_sizes(1 << 16, seed=5).astype(np.float64).mean())
+    assert abs(mean - 1636.8) < 60                       # the note's mean block, k uniform in [4, 13]
+    assert "within L2" in bench.l2_note(1 << 16)
