@@ -2415,13 +2415,20 @@ __device__ __forceinline__ void *stage_malloc(ouro_block_ctx<WARPS> &ctx, const 
   return stage_malloc<V, WARPS>(ctx, h, n, want, __activemask());
 }
 
-/* staged free; every lane of mask calls (as stage_malloc) */
+/* staged free; every lane of mask calls (as stage_malloc).  known_cls >= 0:
+ * the caller allocated p itself with that page class (the library's fused
+ * kernels), so the chunk table is not read and p is not checked; only for
+ * page queues outside checked mode. */
 template <int V, int WARPS, bool LOCKED = false>
-__device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p, unsigned mask) {
+__device__ void stage_free(ouro_block_ctx<WARPS> &ctx, const ouro_heap_dev &h, void *p, unsigned mask,
+                           int known_cls = -1) {
   const unsigned lane = laneid(), w = threadIdx.x >> 5;
   unsigned item = 0;
   int cls = -1;
-  if (p) {
+  if (p && known_cls >= 0 && known_cls < (int)h.n_classes && ouro_page_queues(V) && !h.checked) {
+    cls = known_cls;
+    item = (unsigned)(((const unsigned char *)p - h.base) >> (4 + cls));
+  } else if (p) {
     cls = locate(h, p, &item);
     if (cls < 0) set_error(h, OURO_ERR_BAD_FREE, OURO_SITE_BAD_FREE);
     else if (cls >= (int)h.n_classes) {

@@ -410,7 +410,9 @@ __global__ void __launch_bounds__(256, ouro_page_queues(V) ? OURO_FUSED_MIN_BLOC
     __syncwarp();
     warp_payload<PAY_FUSED>(p, sz, (uint32_t)i, seed, mode, a);
     __syncwarp();
-    if (STAGE) stage_free_v<V>(ctx, h, p);
+    /* staged: the class of each block is known here, so the free skips the
+     * chunk-table lookup (one L2 round trip per task off the warp's chain) */
+    if (STAGE) ouro::detail::stage_free<V, 8>(ctx, h, p, __activemask(), p ? size_class(h, sz) : -1);
     else if (i < n) free_v<V>(h, p);
     __syncwarp();
   }
